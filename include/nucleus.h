@@ -1,0 +1,149 @@
+/*
+ * nucleus.h -- C-ABI of libnucleus, a GB300 (sm_103a) implementation of exact and approximate
+ * hierarchical (r,s) nucleus decomposition.
+ *
+ * Paper: J. Shi, L. Dhulipala, J. Shun, "Parallel Algorithms for Hierarchical Nucleus
+ * Decomposition" (arXiv 2306.08623).  The path is the interleaved framework of Alg. 3 with
+ * link-efficient / construct-tree-efficient (Alg. 5), and the approximate peel of Alg. 2.
+ *
+ * Conventions for every entry point
+ *  - Graph input: an undirected simple graph in CSR form in DEVICE memory: off[n+1] (int64,
+ *    off[0] = 0, off[n] = 2m) and adj[2m] (int32); every neighbour list sorted ascending, no
+ *    self-loops, no duplicate edges.  The caller owns these buffers and must keep them alive and
+ *    unchanged while any handle built from them exists.
+ *  - Every other array argument is a DEVICE pointer owned by the caller, unless it is marked
+ *    "host".  Handles (nh_oriented, nh_rindex) are opaque, allocated by the library with
+ *    stream-ordered device allocations and released by the matching *_free call.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Work is enqueued on
+ *    it; an entry point that returns a host value (counts, statistics) synchronises the stream
+ *    before returning.  No entry point aborts, traps or prints.
+ *  - r-clique ids: the canonical order is lexicographic by the sorted vertex tuple, so id i of
+ *    (r=1) is vertex i, of (r=2) the i-th edge (u<v) in lexicographic order, of (r=3) the i-th
+ *    triangle (a<b<c) in lexicographic order.
+ *  - Supported (r,s): (1,2), (1,3), (2,3), (2,4), (3,4).  Others return NH_ERR_UNSUPPORTED.
+ *  - Counts and core numbers are uint32; the configurations stay far below 2^32.
+ *  - Return value: NH_OK (0) or one of the NH_ERR_* codes below.  A code returned by a device-side
+ *    check (table full, bounded wait expired, bad index) leaves the context usable.
+ */
+#ifndef NUCLEUS_H
+#define NUCLEUS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NH_OK 0
+#define NH_ERR_INVALID 1      /* bad argument, null pointer, unsupported graph layout         */
+#define NH_ERR_OOM 2          /* a device allocation failed                                   */
+#define NH_ERR_TABLE_FULL 3   /* the r-clique hash table ran out of slots                      */
+#define NH_ERR_OVERFLOW 4     /* an internal work queue overflowed                            */
+#define NH_ERR_TIMEOUT 5      /* a bounded device wait (grid barrier, CAS retry) expired       */
+#define NH_ERR_UNSUPPORTED 6  /* (r,s) outside the supported set                              */
+#define NH_ERR_CUDA 7         /* a CUDA runtime call failed                                   */
+#define NH_ERR_INTERNAL 8     /* a device-side consistency check failed (lookup miss)          */
+
+typedef struct nh_oriented nh_oriented;
+typedef struct nh_rindex nh_rindex;
+
+/* Peel statistics, written to host memory when the pointer is not NULL. */
+typedef struct nh_peel_stats {
+  uint64_t rounds;             /* peeling rounds (rho of §5 for the exact peel)                */
+  uint64_t levels;             /* rounds that opened a new level / bucket by a full scan       */
+  uint32_t kmax;               /* largest core number (exact) or largest value (approx)        */
+  uint32_t reserved;
+  uint64_t s_cliques_listed;   /* (R, S) pairs re-listed over the whole peel                   */
+  uint64_t decrements;         /* count decrements applied                                     */
+  uint64_t link_calls;         /* link-efficient invocations including cascades               */
+  uint64_t unites;             /* successful union-find unions                                 */
+  uint64_t scan_elements;      /* adjacency entries scanned while re-listing                   */
+  uint64_t hash_probes;        /* r-clique hash look-ups (r = 3)                               */
+  uint64_t frontier_total;     /* sum of frontier sizes                                        */
+  uint64_t overflow_links;     /* link calls deferred to the device overflow queue             */
+} nh_peel_stats;
+
+/* a1 -- Arb-Orient (Alg. 3, first step; §3 on O(alpha)-orientations).
+ * Builds the low out-degree orientation: u -> v iff (deg u, u) < (deg v, v) lexicographically;
+ * out-lists keep ascending vertex order.  Also builds, per adjacency entry, the canonical id of
+ * its edge, and the lexicographic edge list.  n >= 1; nnz = off[n] = 2m (read from the host
+ * copy of off[n] the caller passes as nnz).  Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_CUDA. */
+int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, const int32_t* adj,
+                         nh_oriented** out, void* stream);
+/* host outputs: vertices, undirected edges, largest out-degree, largest degree */
+int nh_oriented_info(const nh_oriented* o, int64_t* n, int64_t* m, int64_t* max_out, int64_t* max_deg);
+void nh_oriented_free(nh_oriented* o);
+
+/* a2 -- index the r-cliques (the keys of table U in Alg. 3).  r = 1: vertices; r = 2: edges;
+ * r = 3: triangles, enumerated per lexicographic edge (a,b) as the common neighbours c > b, and
+ * inserted into a device open-addressing hash table keyed by (edge id of (a,b), c).
+ * *n_r (host) receives the number of r-cliques.
+ * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_TABLE_FULL, NH_ERR_CUDA. */
+int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, int64_t* n_r, void* stream);
+/* write the vertex tuples of all r-cliques, tuples[i*r + j] (int32, device, n_r*r entries) */
+int nh_rindex_tuples(const nh_rindex* ri, int32_t* tuples, void* stream);
+void nh_rindex_free(nh_rindex* ri);
+
+/* a3 -- rec-list-cliques (Alg. 3, count step): cnt[R] = number of s-cliques containing R
+ * (s-clique-degree, §3), for every r-clique R, found by recursive intersection of out-lists of
+ * the orientation so that each s-clique is listed once.  cnt: uint32[n_r] (overwritten).
+ * *n_s (host, may be NULL) receives the number of s-cliques.
+ * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_INTERNAL, NH_ERR_CUDA. */
+int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt,
+                       uint64_t* n_s, void* stream);
+
+/* a4-a8 -- the peeling loop of Alg. 3 interleaved with link-efficient (Alg. 5), in one
+ * persistent cooperative kernel.  Round t: k = max(k, min count over live r-cliques); the
+ * frontier A is every live r-clique with count <= k; each R in A re-lists its s-cliques; an
+ * s-clique whose members were all live at the start of the round dies now: its member of least
+ * id in A decrements the other live members once and links the members of A in it; an
+ * s-clique that died in an earlier round is linked from R to one of its earlier-peeled members
+ * of least core (link_mode 0, the definition of §3) -- link_mode 1 instead links R with every
+ * member peeled no later than R (the literal pair rule of Alg. 3).
+ * Inputs: cnt uint32[n_r] (s-clique-degrees, not modified).
+ * Outputs: core uint32[n_r] (exact (r,s)-clique core numbers), round uint32[n_r] (1-based peel
+ * round), uf int32[n_r] and L int32[n_r] (the union-find and nearest-lower-core table of
+ * Alg. 5; -1 = empty).  round and uf/L are required.
+ * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_TIMEOUT, NH_ERR_OVERFLOW,
+ * NH_ERR_INTERNAL, NH_ERR_CUDA. */
+int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt,
+                     uint32_t* core, uint32_t* round, int32_t* uf, int32_t* L, int link_mode,
+                     nh_peel_stats* stats, void* stream);
+
+/* a9 -- construct-tree-efficient (Alg. 5): one node per union-find component, its parent the
+ * node of find(L[root]); a node whose subtree holds a single r-clique is dropped and that
+ * r-clique hangs from the dropped node's parent (§7.3 remark on single-child parents).
+ * uf is compressed in place.  Outputs: parent int32[n_r + n_nodes] (entries 0..n_r-1: node of
+ * each r-clique or -1; entries n_r + j: parent node of node j or -1) -- the caller passes room
+ * for 2*n_r entries; label uint32[n_r] (label[j] = level of node j); *n_nodes (host).
+ * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_CUDA. */
+int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
+                      int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
+
+/* a10 -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
+ * x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta) (IEEE double, C = binom(s,r)); round t peels
+ * every live r-clique with count <= t_i; after T = ceil(ln(max(n_r,2)) / log1p(delta/C)) + 1
+ * rounds in one bucket, or when it is empty, the next bucket opens.  approx[R] = min(t_i,
+ * cnt[R]) for the bucket it is peeled in.  Outputs approx uint32[n_r], round uint32[n_r].
+ * delta > 0.  Errors as nh_peel_and_link. */
+int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double delta,
+                      const uint32_t* cnt, uint32_t* approx, uint32_t* round,
+                      nh_peel_stats* stats, void* stream);
+
+/* link-efficient (Alg. 5) applied to a batch of calls, one device thread per call, all
+ * concurrent: pairs int32[2*n_pairs] (R, Q), core uint32[n_r] (ND), uf / L int32[n_r] updated
+ * in place.  The building block of nh_peel_and_link, exported for direct use and testing.
+ * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_TIMEOUT, NH_ERR_OVERFLOW, NH_ERR_CUDA. */
+int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L,
+                  const int32_t* pairs, int64_t n_pairs, void* stream);
+
+/* static description of a status code (never NULL) */
+const char* nh_status_string(int status);
+/* library version: major*10000 + minor*100 + patch */
+int nh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUCLEUS_H */

@@ -1,0 +1,19 @@
+// nh_api.cu -- status strings and version of the C-ABI (the entry points live beside their kernels).
+#include "nh_internal.cuh"
+
+extern "C" const char* nh_status_string(int status) {
+  switch (status) {
+    case NH_OK: return "ok";
+    case NH_ERR_INVALID: return "invalid argument";
+    case NH_ERR_OOM: return "device allocation failed";
+    case NH_ERR_TABLE_FULL: return "r-clique hash table full";
+    case NH_ERR_OVERFLOW: return "device work queue overflow";
+    case NH_ERR_TIMEOUT: return "bounded device wait expired";
+    case NH_ERR_UNSUPPORTED: return "unsupported (r,s) or device";
+    case NH_ERR_CUDA: return "CUDA runtime error";
+    case NH_ERR_INTERNAL: return "device consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int nh_version(void) { return 100; }

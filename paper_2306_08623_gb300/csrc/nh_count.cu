@@ -1,0 +1,231 @@
+// nh_count.cu -- a3: rec-list-cliques.  Every s-clique is listed once, from its lowest-ranked
+// vertex v and its out-neighbour a (one warp per out-edge (v -> a)), by intersecting sorted
+// out-lists; the s-clique-degree of each of its binom(s,r) r-subsets is incremented.
+#include "nh_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarpsPerBlock = kThreads / 32;
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(NH_FULL, v, d);
+  return v;
+}
+
+__device__ __forceinline__ void tri_add(const GView& g, unsigned long long key, uint32_t inc, uint32_t* cnt,
+                                        int* status) {
+  int64_t id = nh_tri_lookup(g.table, g.mask, key);
+  if (id < 0) { atomicExch(status, NH_ERR_INTERNAL); return; }
+  atomicAdd(&cnt[id], inc);
+}
+
+// (1,2): the s-clique-degree of a vertex is its degree
+__global__ void k_count_12(int64_t n, const int64_t* __restrict__ off, uint32_t* __restrict__ cnt) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    cnt[v] = (uint32_t)(off[v + 1] - off[v]);
+}
+
+// s = 3: triangles (v, a, b) with a, b in N+(v), b in N+(a)
+template <int R>
+__global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long found = 0;
+  for (int64_t p = warp; p < g.m; p += nwarps) {
+    const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
+    int64_t sb = g.ooff[v], se = g.ooff[v + 1];  // scanned list
+    int64_t lb = g.ooff[a], le = g.ooff[a + 1];  // searched list
+    const bool scan_v = (se - sb) <= (le - lb);
+    if (!scan_v) {
+      int64_t t0 = sb, t1 = se;
+      sb = lb; se = le; lb = t0; le = t1;
+    }
+    uint32_t tot = 0;
+    for (int64_t j = sb + lane; j < se; j += 32) {
+      const int32_t b = g.oadj[j];
+      const int64_t q = nh_find(g.oadj, lb, le, b);
+      if (q < 0) continue;
+      tot++;
+      const int32_t e_vb = g.oeid[scan_v ? j : q], e_ab = g.oeid[scan_v ? q : j];
+      if (R == 1) atomicAdd(&cnt[b], 1u);
+      if (R == 2) { atomicAdd(&cnt[e_vb], 1u); atomicAdd(&cnt[e_ab], 1u); }
+    }
+    tot = warp_sum(tot);
+    if (lane == 0 && tot) {
+      if (R == 1) { atomicAdd(&cnt[v], tot); atomicAdd(&cnt[a], tot); }
+      if (R == 2) atomicAdd(&cnt[e_va], tot);
+      found += tot;
+    }
+  }
+  if (lane == 0 && found) atomicAdd(n_s, found);
+}
+
+// s = 4: 4-cliques (v, a, b, c): C2 = N+(v) n N+(a) is staged per warp (in shared memory when it
+// fits, else in a global per-warp slice); c runs over N+(b) and is searched in C2.
+template <int R>
+__global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
+                           int32_t* __restrict__ gscratch, int cap, int use_smem, int* __restrict__ status) {
+  extern __shared__ int32_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* base = use_smem ? smem + (size_t)wib * 3 * cap : gscratch + (size_t)warp * 3 * cap;
+  int32_t* c2v = base;
+  int32_t* c2e1 = base + cap;  // edge (v, b)
+  int32_t* c2e2 = base + 2 * cap;  // edge (a, b)
+  unsigned long long found = 0;
+  for (int64_t p = warp; p < g.m; p += nwarps) {
+    const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
+    int64_t sb = g.ooff[v], se = g.ooff[v + 1];
+    int64_t lb = g.ooff[a], le = g.ooff[a + 1];
+    const bool scan_v = (se - sb) <= (le - lb);
+    if (!scan_v) {
+      int64_t t0 = sb, t1 = se;
+      sb = lb; se = le; lb = t0; le = t1;
+    }
+    int n2 = 0;
+    for (int64_t base_j = sb; base_j < se; base_j += 32) {
+      const int64_t j = base_j + lane;
+      int64_t q = -1;
+      int32_t b = 0;
+      if (j < se) {
+        b = g.oadj[j];
+        q = nh_find(g.oadj, lb, le, b);
+      }
+      const unsigned msk = __ballot_sync(NH_FULL, q >= 0);
+      if (q >= 0) {
+        const int k = n2 + __popc(msk & ((1u << lane) - 1u));
+        c2v[k] = b;
+        c2e1[k] = g.oeid[scan_v ? j : q];
+        c2e2[k] = g.oeid[scan_v ? q : j];
+      }
+      n2 += __popc(msk);
+    }
+    __syncwarp();
+    uint32_t tot_item = 0;
+    for (int i = 0; i < n2; i++) {
+      const int32_t b = c2v[i], e_vb = c2e1[i], e_ab = c2e2[i];
+      const int64_t bb = g.ooff[b], be = g.ooff[b + 1];
+      uint32_t n3 = 0;
+      for (int64_t j = bb + lane; j < be; j += 32) {
+        const int32_t c = g.oadj[j];
+        // binary search c in c2v[i+1 .. n2): c must follow b in C2 (sorted) since both are
+        // out-neighbours of v and ids are sorted; search the whole tail
+        int lo = i + 1, hi = n2;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (c2v[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        int k = (lo < n2 && c2v[lo] == c) ? lo : -1;
+        if (k < 0) {
+          // c may precede b in id order; search the head as well
+          lo = 0; hi = i;
+          while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (c2v[mid] < c) lo = mid + 1; else hi = mid;
+          }
+          k = (lo < i && c2v[lo] == c) ? lo : -1;
+        }
+        if (k < 0) continue;
+        n3++;
+        const int32_t e_vc = c2e1[k], e_ac = c2e2[k], e_bc = g.oeid[j];
+        if (R == 1) atomicAdd(&cnt[c], 1u);
+        if (R == 2) { atomicAdd(&cnt[e_vc], 1u); atomicAdd(&cnt[e_ac], 1u); atomicAdd(&cnt[e_bc], 1u); }
+        if (R == 3) {
+          tri_add(g, nh_tri_key(v, a, c, e_va, e_vc, e_ac), 1u, cnt, status);
+          tri_add(g, nh_tri_key(v, b, c, e_vb, e_vc, e_bc), 1u, cnt, status);
+          tri_add(g, nh_tri_key(a, b, c, e_ab, e_ac, e_bc), 1u, cnt, status);
+        }
+      }
+      n3 = warp_sum(n3);
+      if (lane == 0 && n3) {
+        if (R == 1) atomicAdd(&cnt[b], n3);
+        if (R == 2) { atomicAdd(&cnt[e_vb], n3); atomicAdd(&cnt[e_ab], n3); }
+        if (R == 3) tri_add(g, nh_tri_key(v, a, b, e_va, e_vb, e_ab), n3, cnt, status);
+      }
+      tot_item += n3;
+    }
+    if (lane == 0 && tot_item) {
+      if (R == 1) { atomicAdd(&cnt[v], tot_item); atomicAdd(&cnt[a], tot_item); }
+      if (R == 2) atomicAdd(&cnt[e_va], tot_item);
+      found += tot_item;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && found) atomicAdd(n_s, found);
+}
+
+int grid_for(const void* fn, int threads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+}  // namespace
+
+extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
+                                  void* stream) {
+  if (!o || !ri || !cnt || ri->o != o) return NH_ERR_INVALID;
+  const int r = ri->r;
+  if (!nh_supported(r, s) && !(r == 1 && s == 4)) return NH_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  GView g = make_view(o, ri);
+  if (r == 1 && s == 2) {
+    k_count_12<<<nh_blocks_for(o->n, 256, 152 * 32), 256, 0, st>>>(o->n, o->off, cnt);
+    if (cudaGetLastError() != cudaSuccess) return NH_ERR_CUDA;
+    if (n_s) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return NH_ERR_CUDA;
+      *n_s = (uint64_t)o->m;
+    }
+    return NH_OK;
+  }
+  unsigned long long* dcount = nullptr;
+  int* status = nullptr;
+  int32_t* scratch = nullptr;
+  int rc = NH_OK;
+  if ((rc = nh_alloc(&dcount, 1, st)) || (rc = nh_alloc(&status, 1, st))) {
+    nh_free(dcount, st); nh_free(status, st);
+    return rc;
+  }
+  cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ri->n_r, st);
+  if (s == 3) {
+    const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
+    int grid = grid_for(fn, kThreads, 0);
+    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
+    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
+  } else {
+    const int cap = (int)(o->max_out > 0 ? o->max_out : 1);
+    const size_t smem = (size_t)kWarpsPerBlock * 3 * cap * sizeof(int32_t);
+    const int use_smem = smem <= 200 * 1024;
+    const void* fn = (r == 1) ? (const void*)k_count_s4<1> : (r == 2) ? (const void*)k_count_s4<2> : (const void*)k_count_s4<3>;
+    if (use_smem) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = grid_for(fn, kThreads, use_smem ? smem : 0);
+    if (!use_smem && (rc = nh_alloc(&scratch, (int64_t)grid * kWarpsPerBlock * 3 * cap, st))) {
+      nh_free(dcount, st); nh_free(status, st);
+      return rc;
+    }
+    const size_t dyn = use_smem ? smem : 0;
+    if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
+    else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
+    else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
+  }
+  if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+  unsigned long long hcount = 0;
+  int hs = 0;
+  cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  if (!rc && hs) rc = hs;
+  if (!rc && n_s) *n_s = hcount;
+  return rc;
+}

@@ -1,0 +1,193 @@
+// nh_internal.cuh -- shared internals of libnucleus (device helpers, handle layouts).
+//
+// Data layout in HBM (all int32 unless noted):
+//   CSR             off[n+1] (int64), adj[2m]                         caller-owned
+//   eid[2m]         canonical (lexicographic) edge id of every adjacency entry
+//   ooff[n+1] (i64), oadj[m], oeid[m], osrc[m]   out-CSR of the degree orientation, the edge id and
+//                   the source vertex of every out-entry
+//   uoff[n+1] (i64) first lexicographic edge id of each vertex (edges (u,v), u<v)
+//   eu[m], ev[m]    endpoints of edge id e (eu < ev)
+//   tri[3 n_r]      vertices of triangle id t (r = 3), toff[m+1] (i64) first triangle id per edge
+//   table[cap]      16-byte slots {key u64, id u32, pad}: key = (edge id of (a,b)) << 32 | c
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nucleus.h"
+
+#define NH_FULL 0xffffffffu
+#define NH_EMPTY_KEY 0xffffffffffffffffull
+
+struct nh_slot {
+  unsigned long long key;
+  uint32_t val;
+  uint32_t pad;
+};
+
+struct nh_oriented {
+  int64_t n, m;
+  const int64_t* off;
+  const int32_t* adj;
+  int32_t* eid;
+  int64_t* ooff;
+  int32_t* oadj;
+  int32_t* oeid;
+  int32_t* osrc;
+  int64_t* uoff;
+  int32_t* eu;
+  int32_t* ev;
+  int64_t max_out, max_deg;
+  cudaStream_t stream;  // stream the handle was built on (frees are ordered on it)
+};
+
+struct nh_rindex {
+  int r;
+  int64_t n_r;
+  const nh_oriented* o;
+  int32_t* tri;
+  int64_t* toff;
+  nh_slot* table;
+  unsigned long long mask;
+  cudaStream_t stream;
+};
+
+// Read-only view of the graph, passed to kernels by value.
+struct GView {
+  const int64_t* off;
+  const int32_t* adj;
+  const int32_t* eid;
+  const int64_t* ooff;
+  const int32_t* oadj;
+  const int32_t* oeid;
+  const int32_t* osrc;
+  const int32_t* eu;
+  const int32_t* ev;
+  const int32_t* tri;
+  const nh_slot* table;
+  unsigned long long mask;
+  int64_t n, m;
+};
+
+static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
+  GView g;
+  g.off = o->off; g.adj = o->adj; g.eid = o->eid;
+  g.ooff = o->ooff; g.oadj = o->oadj; g.oeid = o->oeid; g.osrc = o->osrc;
+  g.eu = o->eu; g.ev = o->ev;
+  g.tri = ri ? ri->tri : nullptr;
+  g.table = ri ? ri->table : nullptr;
+  g.mask = ri ? ri->mask : 0ull;
+  g.n = o->n; g.m = o->m;
+  return g;
+}
+
+// ---------------------------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------------------------
+
+// first index p in [lo, hi) with a[p] >= x (a sorted ascending)
+__device__ __forceinline__ int64_t nh_lower_bound(const int32_t* __restrict__ a, int64_t lo, int64_t hi,
+                                                  int32_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// position of x in a[lo, hi) or -1
+__device__ __forceinline__ int64_t nh_find(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
+  int64_t p = nh_lower_bound(a, lo, hi, x);
+  return (p < hi && __ldg(a + p) == x) ? p : -1;
+}
+
+// SplitMix64 finalizer (Steele, Lea, Flood 2014) as the hash of a 64-bit key.
+__device__ __forceinline__ unsigned long long nh_mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+// Key of triangle {x, y, z} given the edge ids of its three pairs: the edge id of the two
+// smaller vertices, shifted up, and the largest vertex.
+__device__ __forceinline__ unsigned long long nh_tri_key(int32_t x, int32_t y, int32_t z, int32_t exy,
+                                                         int32_t exz, int32_t eyz) {
+  if (x > y && x > z) return ((unsigned long long)(uint32_t)eyz << 32) | (uint32_t)x;
+  if (y > z) return ((unsigned long long)(uint32_t)exz << 32) | (uint32_t)y;
+  return ((unsigned long long)(uint32_t)exy << 32) | (uint32_t)z;
+}
+
+// Triangle id for a key, or -1 when absent.  Linear probing with a probe cap of the table size.
+__device__ __forceinline__ int64_t nh_tri_lookup(const nh_slot* __restrict__ t, unsigned long long mask,
+                                                 unsigned long long key) {
+  unsigned long long h = nh_mix64(key) & mask;
+  for (unsigned long long p = 0; p <= mask; ++p) {
+    ulonglong2 s = __ldg(reinterpret_cast<const ulonglong2*>(t + h));
+    if (s.x == key) return (int64_t)(uint32_t)s.y;
+    if (s.x == NH_EMPTY_KEY) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ unsigned long long nh_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int32_t nh_ld_volatile(const int32_t* p) { return *(const volatile int32_t*)p; }
+__device__ __forceinline__ uint32_t nh_ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+// host-side launch helpers
+#define NH_CUDA_TRY(x)                      \
+  do {                                      \
+    cudaError_t _e = (x);                   \
+    if (_e != cudaSuccess) {                \
+      (void)cudaGetLastError();             \
+      return (_e == cudaErrorMemoryAllocation) ? NH_ERR_OOM : NH_ERR_CUDA; \
+    }                                       \
+  } while (0)
+
+static inline unsigned nh_blocks_for(int64_t n, int threads, int64_t cap = 1 << 20) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
+int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// allocation helpers (stream ordered)
+template <typename T>
+static inline int nh_alloc(T** p, int64_t count, cudaStream_t st) {
+  *p = nullptr;
+  size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  cudaError_t e = cudaMallocAsync((void**)p, bytes, st);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return NH_ERR_OOM;
+  }
+  return NH_OK;
+}
+template <typename T>
+static inline void nh_free(T* p, cudaStream_t st) {
+  if (p) (void)cudaFreeAsync((void*)p, st);
+}
+
+static inline int nh_binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  int b = 1;
+  for (int i = 1; i <= k; i++) b = b * (n - k + i) / i;
+  return b;
+}
+
+static inline bool nh_supported(int r, int s) {
+  return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
+}

@@ -1,0 +1,855 @@
+// nh_peel.cu -- a4..a8 and a10: the peeling loop of Alg. 3 (exact, interleaved with
+// link-efficient of Alg. 5) and of Alg. 2 (approximate), as one persistent cooperative kernel
+// per call; plus link-efficient on a batch of calls (nh_link_pairs).
+//
+// Round t of the loop (all blocks run it in lockstep, separated by a bounded grid barrier whose
+// last arriving block updates the shared control block):
+//   frontier A  -- either the r-cliques whose count crossed to <= threshold during round t-1
+//                  (kept exactly: a decrement that takes a count from thr+1 to thr appends it),
+//                  or, when that set is empty (new level) or the approximate bucket changes, a
+//                  scan of the compacted live list: threshold = max(k, min count) (exact) or the
+//                  first bucket end >= min count (approx), A = live with count <= threshold.
+//   re-listing  -- one warp per R in A: candidates are the common neighbours of R's vertices
+//                  (the shortest adjacency list is scanned, the others binary-searched), then
+//                  (s-r)-cliques among them through the orientation; for each s-clique S the
+//                  other members' ids come from the adjacency positions (edge ids) or the
+//                  triangle hash table.
+//   per (R, S)  -- S is dead if a member was peeled in an earlier round (round stamp in [1,t));
+//                  otherwise the member of least id among S n A decrements the live members once
+//                  (each s-clique dies exactly once) and links S n A; a dead S links R with an
+//                  earlier-peeled member of least core (that member's core is min core over S).
+// round[] stamps: 0 = never peeled, t = peeled in round t; an r-clique that crosses during round
+// t is stamped t+1 at once, which every reader of round t treats as live.
+#include <cmath>
+#include <vector>
+
+#include "nh_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kLinkStack = 16;
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct PeelCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int err;
+  int done;
+  unsigned int t;
+  unsigned int thr;
+  unsigned int bucket;
+  unsigned int rounds_in_bucket;
+  unsigned int need_scan;
+  unsigned int cur;
+  unsigned int alive_cur;
+  unsigned int gmin;
+  unsigned int draining;
+  unsigned int drain_buf;
+  unsigned int ovf_cur;
+  unsigned int kmax;
+  unsigned long long finished;
+  unsigned long long fsize;
+  unsigned long long nf_count;
+  unsigned long long alive_n;
+  unsigned long long alive2_count;
+  unsigned long long f_count;
+  unsigned long long drain_n;
+  unsigned long long ovf_count[2];
+  // statistics
+  unsigned long long st_rounds, st_levels, st_listed, st_dec, st_link, st_unite, st_scan, st_probe, st_front,
+      st_ovf;
+};
+
+struct LinkEnv {
+  int32_t* uf;
+  int32_t* L;
+  const uint32_t* core;
+  int2* ovf[2];
+  unsigned long long ovf_cap;
+  PeelCtl* ctl;
+};
+
+struct PeelArgs {
+  GView g;
+  int64_t n_r;
+  uint32_t* cnt;          // working counts
+  const uint32_t* cnt0;   // s-clique-degrees
+  uint32_t* val;          // core (exact) or approximate value
+  uint32_t* round;
+  int32_t* alive[2];
+  int32_t* front[2];
+  const uint32_t* thresholds;
+  int n_thr;
+  uint32_t T;
+  int link_mode;          // 0 definitional, 1 pairwise, -1 none
+  int stats;
+  unsigned long long timeout_ns;
+  LinkEnv lk;
+};
+
+struct LocalStats {
+  unsigned long long listed, dec, link, unite, scan, probe, ovf;
+};
+
+// ---------------------------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = min(v, __shfl_xor_sync(NH_FULL, v, d));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(NH_FULL, v, d);
+  return v;
+}
+
+// warp-aggregated append; every lane of the warp must call it
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long* counter, bool pred, int lane) {
+  const unsigned m = __ballot_sync(NH_FULL, pred);
+  if (!m) return 0;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(NH_FULL, base, leader);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Grid barrier with a bounded wait.  The last block to arrive runs `leader` (thread 0) before
+// releasing the others.  Returns false once any block has recorded an error.
+template <class F>
+__device__ __forceinline__ bool grid_sync(PeelCtl* ctl, unsigned long long timeout_ns, F leader) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile PeelCtl* vc = ctl;
+    const unsigned int gen = vc->bar_gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      __threadfence();
+      leader();
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = nh_globaltimer();
+      while (vc->bar_gen == gen) {
+        __nanosleep(64);
+        if (nh_globaltimer() - t0 > timeout_ns) {
+          atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = (vc->err == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// concurrent union-find (CAS, path halving) and link-efficient (Alg. 5)
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int32_t uf_find(int32_t* uf, int32_t x) {
+  // parent ids strictly decrease along a path, so this ends; the cap is only a guard
+  for (int it = 0; it < (1 << 24); ++it) {
+    const int32_t p = __ldcg(uf + x);
+    if (p == x) return x;
+    const int32_t gp = __ldcg(uf + p);
+    if (gp != p) atomicCAS(uf + x, p, gp);
+    x = gp;
+  }
+  return x;
+}
+
+// unite the sets of a and b: the root of larger id is hung under the root of smaller id
+__device__ __forceinline__ bool uf_unite(int32_t* uf, int32_t a, int32_t b, PeelCtl* ctl) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    a = uf_find(uf, a);
+    b = uf_find(uf, b);
+    if (a == b) return false;
+    if (a < b) { const int32_t t = a; a = b; b = t; }
+    if (atomicCAS(uf + a, a, b) == a) {
+      __threadfence();
+      return true;
+    }
+  }
+  atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void ovf_push(const LinkEnv& E, int32_t a, int32_t b, LocalStats& ls) {
+  const unsigned int cur = *(volatile unsigned int*)&E.ctl->ovf_cur;
+  const unsigned long long pos = atomicAdd(&E.ctl->ovf_count[cur], 1ull);
+  if (pos < E.ovf_cap) E.ovf[cur][pos] = make_int2(a, b);
+  else atomicCAS(&E.ctl->err, 0, NH_ERR_OVERFLOW);
+  ls.ovf++;
+}
+
+// link-efficient(R0, Q0) of Alg. 5 with the recursion replaced by a small per-thread stack; calls
+// that do not fit go to the overflow queue, drained after the round.
+__device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& ls) {
+  int32_t sR[kLinkStack], sQ[kLinkStack];
+  int sp = 0;
+  sR[0] = R0; sQ[0] = Q0; sp = 1;
+  auto push = [&](int32_t a, int32_t b) {
+    if (a < 0 || b < 0) return;
+    if (sp < kLinkStack) { sR[sp] = a; sQ[sp] = b; ++sp; }
+    else ovf_push(E, a, b, ls);
+  };
+  unsigned int guard = 0;
+  while (sp > 0) {
+    if (++guard > (1u << 22)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
+    --sp;
+    int32_t R = sR[sp], Q = sQ[sp];
+    if (R < 0 || Q < 0) continue;
+    ls.link++;
+    uint32_t nR = __ldcg(E.core + R), nQ = __ldcg(E.core + Q);
+    if (nQ < nR) {
+      const int32_t t = R; R = Q; Q = t;
+      const uint32_t u = nR; nR = nQ; nQ = u;
+    }
+    R = uf_find(E.uf, R);
+    Q = uf_find(E.uf, Q);
+    if (nR == nQ) {
+      if (R != Q && uf_unite(E.uf, R, Q, E.ctl)) ls.unite++;
+      const int32_t pR = uf_find(E.uf, R);
+      if (pR != R) push(__ldcg(E.L + R), pR);
+      const int32_t pQ = uf_find(E.uf, Q);
+      if (pQ != Q) push(__ldcg(E.L + Q), pQ);
+      continue;
+    }
+    // nR < nQ
+    for (unsigned int spin = 0;; ++spin) {
+      if (spin > (1u << 20)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
+      const int32_t LQ = __ldcg(E.L + Q);
+      Q = uf_find(E.uf, Q);
+      if (atomicCAS(E.L + Q, -1, R) == -1) {
+        __threadfence();
+        const int32_t pQ = uf_find(E.uf, Q);
+        if (pQ != Q) push(R, pQ);
+        break;
+      }
+      if (LQ < 0) continue;  // L[Q] was set after our read: retry with the current value
+      if (__ldcg(E.core + LQ) < nR) {
+        if (atomicCAS(E.L + Q, LQ, R) == LQ) {
+          __threadfence();
+          const int32_t pQ = uf_find(E.uf, Q);
+          if (pQ != Q) push(R, pQ);
+          push(R, LQ);
+          break;
+        }
+        continue;
+      }
+      push(R, __ldcg(E.L + Q));
+      break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// per (R, S) step
+// ---------------------------------------------------------------------------------------------
+
+template <bool EXACT>
+__device__ __forceinline__ void dec(const PeelArgs& A, int32_t x, uint32_t t, uint32_t thr, int32_t* nf,
+                                    LocalStats& ls) {
+  const uint32_t old = atomicSub(A.cnt + x, 1u);
+  ls.dec++;
+  if (old == thr + 1u) {
+    const unsigned long long pos = atomicAdd(&A.lk.ctl->nf_count, 1ull);
+    nf[pos] = x;
+    __stcg(A.round + x, t + 1u);
+    __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
+  }
+}
+
+template <int CM, bool EXACT>
+__device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM], uint32_t t,
+                                          uint32_t thr, int32_t* nf, LocalStats& ls) {
+  uint32_t rd[CM];
+  bool dead = false;
+  int32_t attr = Rid;
+#pragma unroll
+  for (int j = 0; j < CM; j++) {
+    rd[j] = __ldcg(A.round + mem[j]);
+    if (rd[j] != 0u && rd[j] < t) dead = true;
+    else if (rd[j] == t && mem[j] < attr) attr = mem[j];
+  }
+  ls.listed++;
+  if (dead) {
+    if (EXACT && A.link_mode == 0) {
+      int32_t best = -1;
+      uint32_t bc = kNone;
+#pragma unroll
+      for (int j = 0; j < CM; j++) {
+        if (rd[j] != 0u && rd[j] < t) {
+          const uint32_t c = __ldcg(A.val + mem[j]);
+          if (c < bc) { bc = c; best = mem[j]; }
+        }
+      }
+      link_run(A.lk, Rid, best, ls);
+    }
+  } else if (attr == Rid) {
+#pragma unroll
+    for (int j = 0; j < CM; j++)
+      if (rd[j] == 0u || rd[j] > t) dec<EXACT>(A, mem[j], t, thr, nf, ls);
+    if (EXACT && A.link_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < CM; j++)
+        if (rd[j] == t) link_run(A.lk, Rid, mem[j], ls);
+    }
+  }
+  if (EXACT && A.link_mode == 1) {
+#pragma unroll
+    for (int j = 0; j < CM; j++)
+      if (rd[j] != 0u && rd[j] <= t) link_run(A.lk, mem[j], Rid, ls);
+  }
+}
+
+__device__ __forceinline__ int32_t tri_id(const PeelArgs& A, unsigned long long key, LocalStats& ls) {
+  ls.probe++;
+  const int64_t id = nh_tri_lookup(A.g.table, A.g.mask, key);
+  if (id < 0) {
+    atomicCAS(&A.lk.ctl->err, 0, NH_ERR_INTERNAL);
+    return 0;
+  }
+  return (int32_t)id;
+}
+
+// ---------------------------------------------------------------------------------------------
+// re-listing of one frontier r-clique by one warp
+// ---------------------------------------------------------------------------------------------
+
+template <int R, int S, bool EXACT>
+__device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
+                            LocalStats& ls) {
+  const GView& g = A.g;
+  int32_t vx[3] = {0, 0, 0};
+  int32_t eR[3] = {0, 0, 0};  // r = 3: edges (v0,v1), (v0,v2), (v1,v2)
+  if (R == 1) {
+    vx[0] = Rid;
+  } else if (R == 2) {
+    vx[0] = __ldg(g.eu + Rid);
+    vx[1] = __ldg(g.ev + Rid);
+  } else {
+    vx[0] = __ldg(g.tri + 3 * (int64_t)Rid);
+    vx[1] = __ldg(g.tri + 3 * (int64_t)Rid + 1);
+    vx[2] = __ldg(g.tri + 3 * (int64_t)Rid + 2);
+    int32_t mine = 0;
+    if (lane < 3) {
+      const int32_t x = (lane == 2) ? vx[1] : vx[0];
+      const int32_t y = (lane == 0) ? vx[1] : vx[2];
+      const int64_t p = nh_find(g.adj, __ldg(g.off + x), __ldg(g.off + x + 1), y);
+      mine = (p >= 0) ? __ldg(g.eid + p) : 0;
+    }
+    eR[0] = __shfl_sync(NH_FULL, mine, 0);
+    eR[1] = __shfl_sync(NH_FULL, mine, 1);
+    eR[2] = __shfl_sync(NH_FULL, mine, 2);
+  }
+  int64_t lo[3], hi[3];
+#pragma unroll
+  for (int i = 0; i < R; i++) {
+    lo[i] = __ldg(g.off + vx[i]);
+    hi[i] = __ldg(g.off + vx[i] + 1);
+  }
+  int best = 0;
+#pragma unroll
+  for (int i = 1; i < R; i++)
+    if (hi[i] - lo[i] < hi[best] - lo[best]) best = i;
+  const int64_t b0 = lo[best], b1 = hi[best];
+  if (lane == 0) ls.scan += (unsigned long long)(b1 - b0);
+  for (int64_t base = b0; base < b1; base += 32) {
+    const int64_t j = base + lane;
+    bool ok = j < b1;
+    int32_t w = 0;
+    int32_t ew[3] = {0, 0, 0};
+    if (ok) {
+      w = __ldg(g.adj + j);
+#pragma unroll
+      for (int i = 0; i < R; i++) {
+        if (i == best) {
+          ew[i] = __ldg(g.eid + j);
+        } else if (ok) {
+          const int64_t p = nh_find(g.adj, lo[i], hi[i], w);
+          if (p < 0) ok = false;
+          else ew[i] = __ldg(g.eid + p);
+        }
+      }
+    }
+    if constexpr (S - R == 1) {
+      if (ok) {
+        if constexpr (R == 1) {
+          const int32_t mem[1] = {w};
+          process_S<1, EXACT>(A, Rid, mem, t, thr, nf, ls);
+        } else if constexpr (R == 2) {
+          const int32_t mem[2] = {ew[0], ew[1]};
+          process_S<2, EXACT>(A, Rid, mem, t, thr, nf, ls);
+        } else {
+          const int32_t mem[3] = {
+              tri_id(A, nh_tri_key(vx[0], vx[1], w, eR[0], ew[0], ew[1]), ls),
+              tri_id(A, nh_tri_key(vx[0], vx[2], w, eR[1], ew[0], ew[2]), ls),
+              tri_id(A, nh_tri_key(vx[1], vx[2], w, eR[2], ew[1], ew[2]), ls)};
+          process_S<3, EXACT>(A, Rid, mem, t, thr, nf, ls);
+        }
+      }
+    } else {
+      // s - r = 2: pairs (w, x), x in N+(w) adjacent to every vertex of R, expanded across the
+      // warp so that lanes share the out-lists of the candidates found in this chunk
+      const uint32_t len = ok ? (uint32_t)(__ldg(g.ooff + w + 1) - __ldg(g.ooff + w)) : 0u;
+      uint32_t incl = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(NH_FULL, incl, d);
+        if (lane >= d) incl += o;
+      }
+      const uint32_t total = __shfl_sync(NH_FULL, incl, 31);
+      for (uint32_t pb = 0; pb < total; pb += 32) {
+        const uint32_t idx = pb + lane;
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const uint32_t v = __shfl_sync(NH_FULL, incl, own + step - 1);
+          if (v <= idx) own += step;
+        }
+        const int32_t ow = __shfl_sync(NH_FULL, w, own);
+        const uint32_t oincl = __shfl_sync(NH_FULL, incl, own);
+        const uint32_t olen = __shfl_sync(NH_FULL, len, own);
+        const int32_t oe0 = __shfl_sync(NH_FULL, ew[0], own);
+        const int32_t oe1 = __shfl_sync(NH_FULL, ew[1], own);
+        if (idx < total) {
+          const int64_t q = __ldg(g.ooff + ow) + (int64_t)(idx - (oincl - olen));
+          const int32_t x = __ldg(g.oadj + q);
+          const int32_t e_wx = __ldg(g.oeid + q);
+          bool okx = true;
+          int32_t ex[2] = {0, 0};
+#pragma unroll
+          for (int i = 0; i < R; i++) {
+            if (!okx) break;
+            const int64_t p = nh_find(g.adj, lo[i], hi[i], x);
+            if (p < 0) okx = false;
+            else ex[i] = __ldg(g.eid + p);
+          }
+          if (okx) {
+            if constexpr (R == 1) {
+              const int32_t mem[2] = {ow, x};
+              process_S<2, EXACT>(A, Rid, mem, t, thr, nf, ls);
+            } else if constexpr (R == 2) {
+              const int32_t mem[5] = {oe0, oe1, ex[0], ex[1], e_wx};
+              process_S<5, EXACT>(A, Rid, mem, t, thr, nf, ls);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------------------------
+
+template <bool EXACT>
+__device__ void leader_after_scan(const PeelArgs& A) {
+  PeelCtl* c = A.lk.ctl;
+  const unsigned int gm = c->gmin;
+  c->gmin = kNone;
+  c->alive_cur ^= 1u;
+  c->alive_n = c->alive2_count;
+  c->alive2_count = 0;
+  c->f_count = 0;
+  if (EXACT) {
+    if (gm != kNone && gm > c->thr) c->thr = gm;
+  } else {
+    while ((int)c->bucket + 1 < A.n_thr && A.thresholds[c->bucket] < gm) {
+      c->bucket++;
+      c->rounds_in_bucket = 0;
+    }
+    c->thr = A.thresholds[c->bucket];
+  }
+  c->st_levels++;
+}
+
+template <bool EXACT>
+__device__ void leader_end_of_round(const PeelArgs& A) {
+  PeelCtl* c = A.lk.ctl;
+  const unsigned int oc = c->ovf_cur;
+  if (c->ovf_count[oc] > 0) {
+    c->draining = 1;
+    c->drain_buf = oc;
+    c->drain_n = c->ovf_count[oc] < A.lk.ovf_cap ? c->ovf_count[oc] : A.lk.ovf_cap;
+    c->ovf_count[oc] = 0;
+    c->ovf_cur = oc ^ 1u;
+    return;
+  }
+  c->draining = 0;
+  c->finished += c->fsize;
+  c->st_rounds++;
+  c->st_front += c->fsize;
+  if (c->thr > c->kmax && c->fsize > 0) c->kmax = c->thr;
+  c->t++;
+  if (c->finished >= (unsigned long long)A.n_r) {
+    c->done = 1;
+    return;
+  }
+  if (!EXACT) {
+    if (++c->rounds_in_bucket >= A.T) {
+      if ((int)c->bucket + 1 < A.n_thr) c->bucket++;
+      c->rounds_in_bucket = 0;
+      c->thr = A.thresholds[c->bucket];
+      c->need_scan = 1;
+      c->nf_count = 0;
+      return;
+    }
+  }
+  if (c->nf_count > 0) {
+    c->cur ^= 1u;
+    c->fsize = c->nf_count;
+    c->nf_count = 0;
+    c->need_scan = 0;
+  } else {
+    c->need_scan = 1;
+  }
+}
+
+template <int R, int S, bool EXACT>
+__global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
+  PeelCtl* ctl = A.lk.ctl;
+  volatile PeelCtl* vc = ctl;
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  for (;;) {
+    if (vc->done || vc->err) break;
+    if (vc->need_scan) {
+      // compact the live list and take the minimum count over it
+      {
+        const unsigned int ac = vc->alive_cur;
+        const int32_t* ain = A.alive[ac];
+        int32_t* aout = A.alive[ac ^ 1u];
+        const unsigned long long na = vc->alive_n;
+        const unsigned int t = vc->t;
+        uint32_t lmin = kNone;
+        for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
+             base += (unsigned long long)nwarps * 32) {
+          const unsigned long long i = base + lane;
+          bool live = false;
+          int32_t x = 0;
+          if (i < na) {
+            x = __ldcg(ain + i);
+            const uint32_t rd = __ldcg(A.round + x);
+            live = (rd == 0u || rd >= t);
+            if (live) lmin = min(lmin, __ldcg(A.cnt + x));
+          }
+          const unsigned long long pos = warp_append(&ctl->alive2_count, live, lane);
+          if (live) aout[pos] = x;
+        }
+        lmin = warp_min_u32(lmin);
+        if (lane == 0 && lmin != kNone) atomicMin(&ctl->gmin, lmin);
+      }
+      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_after_scan<EXACT>(A); })) break;
+      // frontier = live with count <= threshold
+      {
+        const int32_t* al = A.alive[vc->alive_cur];
+        const unsigned long long na = vc->alive_n;
+        const unsigned int thr = vc->thr, t = vc->t;
+        int32_t* fr = A.front[vc->cur];
+        for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
+             base += (unsigned long long)nwarps * 32) {
+          const unsigned long long i = base + lane;
+          bool take = false;
+          int32_t x = 0;
+          if (i < na) {
+            x = __ldcg(al + i);
+            take = __ldcg(A.cnt + x) <= thr;
+          }
+          const unsigned long long pos = warp_append(&ctl->f_count, take, lane);
+          if (take) {
+            fr[pos] = x;
+            __stcg(A.round + x, t);
+            __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
+          }
+        }
+      }
+      if (!grid_sync(ctl, A.timeout_ns, [&] {
+            ctl->fsize = ctl->f_count;
+            ctl->f_count = 0;
+          }))
+        break;
+    }
+    // re-list the frontier
+    {
+      const unsigned int t = vc->t, thr = vc->thr, cur = vc->cur;
+      const unsigned long long fs = vc->fsize;
+      const int32_t* fr = A.front[cur];
+      int32_t* nf = A.front[cur ^ 1u];
+      for (unsigned long long it = (unsigned long long)gwarp; it < fs; it += (unsigned long long)nwarps)
+        relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, ls);
+    }
+    // end of round: drain deferred link calls, then advance
+    bool ok = true;
+    for (;;) {
+      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_end_of_round<EXACT>(A); })) { ok = false; break; }
+      if (!vc->draining) break;
+      const int2* q = A.lk.ovf[vc->drain_buf];
+      const unsigned long long nq = vc->drain_n;
+      for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+           i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 p = __ldcg(q + i);
+        link_run(A.lk, p.x, p.y, ls);
+      }
+    }
+    if (!ok) break;
+  }
+  if (A.stats) {
+    const unsigned long long v0 = warp_sum_u64(ls.listed), v1 = warp_sum_u64(ls.dec), v2 = warp_sum_u64(ls.link),
+                             v3 = warp_sum_u64(ls.unite), v4 = warp_sum_u64(ls.scan), v5 = warp_sum_u64(ls.probe),
+                             v6 = warp_sum_u64(ls.ovf);
+    if (lane == 0) {
+      atomicAdd(&ctl->st_listed, v0);
+      atomicAdd(&ctl->st_dec, v1);
+      atomicAdd(&ctl->st_link, v2);
+      atomicAdd(&ctl->st_unite, v3);
+      atomicAdd(&ctl->st_scan, v4);
+      atomicAdd(&ctl->st_probe, v5);
+      atomicAdd(&ctl->st_ovf, v6);
+    }
+  }
+}
+
+__global__ void k_peel_init(int64_t n_r, const uint32_t* __restrict__ cnt0, uint32_t* __restrict__ cnt,
+                            uint32_t* __restrict__ round, uint32_t* __restrict__ val, int32_t* __restrict__ alive,
+                            int32_t* __restrict__ uf, int32_t* __restrict__ L) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
+    cnt[i] = cnt0[i];
+    round[i] = 0;
+    val[i] = 0;
+    alive[i] = (int32_t)i;
+    if (uf) uf[i] = (int32_t)i;
+    if (L) L[i] = -1;
+  }
+}
+
+__global__ void k_ctl_init(PeelCtl* c, int64_t n_r, unsigned int thr0) {
+  c->t = 1;
+  c->thr = thr0;
+  c->need_scan = 1;
+  c->gmin = kNone;
+  c->alive_n = (unsigned long long)n_r;
+  c->done = (n_r == 0);
+}
+
+__global__ void k_max_u32(int64_t n, const uint32_t* __restrict__ a, unsigned int* __restrict__ out) {
+  unsigned int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, a[i]);
+  m = warp_min_u32(~m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, ~m);
+}
+
+// nh_link_pairs: one thread per call
+__global__ void k_link_pairs(LinkEnv E, const int2* __restrict__ pairs, unsigned long long n) {
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int2 p = pairs[i];
+    link_run(E, p.x, p.y, ls);
+  }
+}
+
+__global__ void k_link_swap(PeelCtl* c, unsigned long long cap) {
+  const unsigned int oc = c->ovf_cur;
+  c->drain_buf = oc;
+  c->drain_n = c->ovf_count[oc] < cap ? c->ovf_count[oc] : cap;
+  c->ovf_count[oc] = 0;
+  c->ovf_cur = oc ^ 1u;
+}
+
+__global__ void k_link_drain(LinkEnv E) {
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  const unsigned int b = E.ctl->drain_buf;
+  const unsigned long long n = E.ctl->drain_n;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int2 p = __ldcg(E.ovf[b] + i);
+    link_run(E, p.x, p.y, ls);
+  }
+}
+
+template <int R, int S, bool EXACT>
+int launch_peel(PeelArgs& A, cudaStream_t st) {
+  const void* fn = (const void*)k_peel<R, S, EXACT>;
+  int dev = 0, sms = 0, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return NH_ERR_UNSUPPORTED;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1)
+    return NH_ERR_CUDA;
+  dim3 grid((unsigned)(sms * per)), block(kThreads);
+  void* args[] = {&A};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st);
+  return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}
+
+template <bool EXACT>
+int dispatch(int r, int s, PeelArgs& A, cudaStream_t st) {
+  if (r == 1 && s == 2) return launch_peel<1, 2, EXACT>(A, st);
+  if (r == 1 && s == 3) return launch_peel<1, 3, EXACT>(A, st);
+  if (r == 2 && s == 3) return launch_peel<2, 3, EXACT>(A, st);
+  if (r == 2 && s == 4) return launch_peel<2, 4, EXACT>(A, st);
+  if (r == 3 && s == 4) return launch_peel<3, 4, EXACT>(A, st);
+  return NH_ERR_UNSUPPORTED;
+}
+
+// shared driver for the exact and the approximate peel
+int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* val,
+             uint32_t* round, int32_t* uf, int32_t* L, int link_mode, double delta, nh_peel_stats* stats,
+             cudaStream_t st) {
+  if (!o || !ri || ri->o != o || !cnt || !val || !round) return NH_ERR_INVALID;
+  const int r = ri->r;
+  if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
+  if (exact && (!uf || !L || link_mode < 0 || link_mode > 1)) return NH_ERR_INVALID;
+  if (!exact && !(delta > 0.0)) return NH_ERR_INVALID;
+  const int64_t n_r = ri->n_r;
+  if (stats) *stats = nh_peel_stats{};
+  if (n_r == 0) return NH_OK;
+  const int C = nh_binom(s, r);
+  PeelArgs A{};
+  A.g = make_view(o, ri);
+  A.n_r = n_r;
+  A.cnt0 = cnt;
+  A.val = val;
+  A.round = round;
+  A.link_mode = exact ? link_mode : -1;
+  A.stats = stats != nullptr;
+  A.timeout_ns = 60ull * 1000000000ull;
+  A.lk.uf = uf;
+  A.lk.L = L;
+  A.lk.core = val;
+  A.lk.ovf_cap = (unsigned long long)(n_r / 4 > (1 << 20) ? n_r / 4 : (1 << 20));
+  int rc = NH_OK;
+  uint32_t* thr_dev = nullptr;
+  unsigned int* dmax = nullptr;
+  std::vector<uint32_t> thr_host;
+  if ((rc = nh_alloc(&A.cnt, n_r, st)) || (rc = nh_alloc(&A.alive[0], n_r, st)) ||
+      (rc = nh_alloc(&A.alive[1], n_r, st)) || (rc = nh_alloc(&A.front[0], n_r, st)) ||
+      (rc = nh_alloc(&A.front[1], n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st))) {
+    goto cleanup;
+  }
+  if (exact) {
+    if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
+      goto cleanup;
+  }
+  if (!exact) {
+    // bucket upper ends t_i = floor(x_i), x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta), up to
+    // the largest count
+    if ((rc = nh_alloc(&dmax, 1, st))) goto cleanup;
+    cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
+    k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, cnt, dmax);
+    unsigned int hmax = 0;
+    cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
+    double x = ((double)C + delta) * (1.0 + delta);
+    for (int i = 0; i < (1 << 16); i++) {
+      const double f = std::floor(x);
+      const uint32_t tv = (f >= 4294967295.0) ? 4294967295u : (uint32_t)f;
+      thr_host.push_back(tv);
+      if (tv >= hmax) break;
+      x = x * (1.0 + delta);
+    }
+    const double nn = (double)(n_r > 2 ? n_r : 2);
+    A.T = (uint32_t)std::ceil(std::log(nn) / std::log1p(delta / (double)C)) + 1u;
+    A.n_thr = (int)thr_host.size();
+    if ((rc = nh_alloc(&thr_dev, A.n_thr, st))) goto cleanup;
+    if (cudaMemcpyAsync(thr_dev, thr_host.data(), sizeof(uint32_t) * thr_host.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
+    A.thresholds = thr_dev;
+  }
+  cudaMemsetAsync(A.lk.ctl, 0, sizeof(PeelCtl), st);
+  k_ctl_init<<<1, 1, 0, st>>>(A.lk.ctl, n_r, exact ? 0u : thr_host[0]);
+  k_peel_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, cnt, A.cnt, round, val, A.alive[0],
+                                                                  exact ? uf : nullptr, exact ? L : nullptr);
+  if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
+  rc = exact ? dispatch<true>(r, s, A, st) : dispatch<false>(r, s, A, st);
+  if (!rc) {
+    PeelCtl h{};
+    cudaMemcpyAsync(&h, A.lk.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
+    else if (h.err) rc = h.err;
+    else if (!h.done) rc = NH_ERR_INTERNAL;
+    if (!rc && stats) {
+      stats->rounds = h.st_rounds;
+      stats->levels = h.st_levels;
+      stats->kmax = h.kmax;
+      stats->s_cliques_listed = h.st_listed;
+      stats->decrements = h.st_dec;
+      stats->link_calls = h.st_link;
+      stats->unites = h.st_unite;
+      stats->scan_elements = h.st_scan;
+      stats->hash_probes = h.st_probe;
+      stats->frontier_total = h.st_front;
+      stats->overflow_links = h.st_ovf;
+    }
+  }
+cleanup:
+  nh_free(A.cnt, st); nh_free(A.alive[0], st); nh_free(A.alive[1], st); nh_free(A.front[0], st);
+  nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
+  nh_free(thr_dev, st); nh_free(dmax, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* core,
+                                uint32_t* round, int32_t* uf, int32_t* L, int link_mode, nh_peel_stats* stats,
+                                void* stream) {
+  return run_peel(true, o, ri, s, cnt, core, round, uf, L, link_mode, 0.0, stats, (cudaStream_t)stream);
+}
+
+extern "C" int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double delta, const uint32_t* cnt,
+                                 uint32_t* approx, uint32_t* round, nh_peel_stats* stats, void* stream) {
+  return run_peel(false, o, ri, s, cnt, approx, round, nullptr, nullptr, -1, delta, stats, (cudaStream_t)stream);
+}
+
+extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L, const int32_t* pairs,
+                             int64_t n_pairs, void* stream) {
+  if (n_r < 0 || n_pairs < 0 || (n_r > 0 && (!core || !uf || !L)) || (n_pairs > 0 && !pairs)) return NH_ERR_INVALID;
+  if (n_pairs == 0) return NH_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  LinkEnv E{};
+  E.uf = uf;
+  E.L = L;
+  E.core = core;
+  E.ovf_cap = (unsigned long long)(n_pairs > (1 << 16) ? n_pairs : (1 << 16));
+  int rc = NH_OK;
+  if ((rc = nh_alloc(&E.ctl, 1, st)) || (rc = nh_alloc(&E.ovf[0], (int64_t)E.ovf_cap, st)) ||
+      (rc = nh_alloc(&E.ovf[1], (int64_t)E.ovf_cap, st))) {
+    nh_free(E.ctl, st); nh_free(E.ovf[0], st); nh_free(E.ovf[1], st);
+    return rc;
+  }
+  cudaMemsetAsync(E.ctl, 0, sizeof(PeelCtl), st);
+  k_link_pairs<<<nh_blocks_for(n_pairs, 128, 152 * 16), 128, 0, st>>>(E, (const int2*)pairs,
+                                                                    (unsigned long long)n_pairs);
+  PeelCtl h{};
+  for (int iter = 0; iter < 1000 && !rc; iter++) {
+    cudaMemcpyAsync(&h, E.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; break; }
+    if (h.err) { rc = h.err; break; }
+    if (h.ovf_count[h.ovf_cur] == 0) break;
+    k_link_swap<<<1, 1, 0, st>>>(E.ctl, E.ovf_cap);
+    k_link_drain<<<152 * 8, 128, 0, st>>>(E);
+  }
+  nh_free(E.ctl, st); nh_free(E.ovf[0], st); nh_free(E.ovf[1], st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  return rc;
+}

@@ -1,0 +1,216 @@
+"""Thin Python binding of libnucleus (argument marshalling only; every step runs in the CUDA
+library).  Device buffers are torch tensors; 32-bit unsigned outputs are returned in int32
+tensors holding the same bit patterns (view them as uint32 on the host).
+
+The binding fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnucleus.so")
+
+SUPPORTED = ((1, 2), (1, 3), (2, 3), (2, 4), (3, 4))
+LINK_MODES = {"def": 0, "pair": 1}
+
+
+class NucleusError(RuntimeError):
+    def __init__(self, where: str, status: int, text: str):
+        super().__init__("%s failed: %s (status %d)" % (where, text, status))
+        self.status = status
+
+
+class PeelStats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64), ("kmax", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32), ("s_cliques_listed", ctypes.c_uint64), ("decrements", ctypes.c_uint64),
+        ("link_calls", ctypes.c_uint64), ("unites", ctypes.c_uint64), ("scan_elements", ctypes.c_uint64),
+        ("hash_probes", ctypes.c_uint64), ("frontier_total", ctypes.c_uint64), ("overflow_links", ctypes.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+_lib = None
+P = ctypes.c_void_p
+I64 = ctypes.c_int64
+I32 = ctypes.c_int
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnucleus.so is not built (run __graft_entry__.build()); no CPU fallback exists")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "nh_build_orientation": (I32, [I64, I64, P, P, ctypes.POINTER(P), P]),
+            "nh_oriented_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                       ctypes.POINTER(I64)]),
+            "nh_oriented_free": (None, [P]),
+            "nh_index_r_cliques": (I32, [P, I32, ctypes.POINTER(P), ctypes.POINTER(I64), P]),
+            "nh_rindex_tuples": (I32, [P, P, P]),
+            "nh_rindex_free": (None, [P]),
+            "nh_count_s_cliques": (I32, [P, P, I32, P, ctypes.POINTER(ctypes.c_uint64), P]),
+            "nh_peel_and_link": (I32, [P, P, I32, P, P, P, P, P, I32, ctypes.POINTER(PeelStats), P]),
+            "nh_construct_tree": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
+            "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
+            "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
+            "nh_status_string": (ctypes.c_char_p, [I32]),
+            "nh_version": (I32, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(where: str, rc: int):
+    if rc != 0:
+        raise NucleusError(where, rc, lib().nh_status_string(rc).decode())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return P(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return P(t.data_ptr())
+
+
+class Oriented:
+    """Degree orientation of a CSR graph held on the device (keeps the CSR tensors alive)."""
+
+    def __init__(self, handle, off, adj):
+        self.handle = handle
+        self.off, self.adj = off, adj
+        n, m, mo, md = I64(), I64(), I64(), I64()
+        _check("nh_oriented_info", lib().nh_oriented_info(handle, ctypes.byref(n), ctypes.byref(m),
+                                                          ctypes.byref(mo), ctypes.byref(md)))
+        self.n, self.m, self.max_out, self.max_deg = n.value, m.value, mo.value, md.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nh_oriented_free(self.handle)
+            self.handle = None
+
+
+class RIndex:
+    def __init__(self, handle, oriented: Oriented, r: int, n_r: int):
+        self.handle, self.oriented, self.r, self.n_r = handle, oriented, r, n_r
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nh_rindex_free(self.handle)
+            self.handle = None
+
+
+def build_orientation(off: torch.Tensor, adj: torch.Tensor, stream=None) -> Oriented:
+    assert off.dtype == torch.int64 and adj.dtype == torch.int32
+    h = P()
+    n = off.numel() - 1
+    _check("nh_build_orientation", lib().nh_build_orientation(n, adj.numel(), _dptr(off), _dptr(adj),
+                                                              ctypes.byref(h), _stream(stream)))
+    return Oriented(h, off, adj)
+
+
+def index_r_cliques(o: Oriented, r: int, stream=None) -> RIndex:
+    h = P()
+    n_r = I64()
+    _check("nh_index_r_cliques", lib().nh_index_r_cliques(o.handle, r, ctypes.byref(h), ctypes.byref(n_r),
+                                                          _stream(stream)))
+    return RIndex(h, o, r, n_r.value)
+
+
+def rindex_tuples(ri: RIndex, stream=None) -> torch.Tensor:
+    out = torch.empty((max(ri.n_r, 1), ri.r), dtype=torch.int32, device="cuda")
+    _check("nh_rindex_tuples", lib().nh_rindex_tuples(ri.handle, _dptr(out), _stream(stream)))
+    return out[: ri.n_r]
+
+
+def count_s_cliques(o: Oriented, ri: RIndex, s: int, cnt: torch.Tensor | None = None, stream=None):
+    if cnt is None:
+        cnt = torch.empty(max(ri.n_r, 1), dtype=torch.int32, device="cuda")
+    n_s = ctypes.c_uint64()
+    _check("nh_count_s_cliques", lib().nh_count_s_cliques(o.handle, ri.handle, s, _dptr(cnt), ctypes.byref(n_s),
+                                                          _stream(stream)))
+    return cnt[: ri.n_r], int(n_s.value)
+
+
+def peel_and_link(o: Oriented, ri: RIndex, s: int, cnt: torch.Tensor, link_mode: str = "def",
+                  stats: bool = False, out: dict | None = None, stream=None) -> dict:
+    n = max(ri.n_r, 1)
+    out = out or {}
+    for key in ("core", "round", "uf", "L"):
+        if key not in out:
+            out[key] = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = PeelStats() if stats else None
+    _check("nh_peel_and_link", lib().nh_peel_and_link(
+        o.handle, ri.handle, s, _dptr(cnt), _dptr(out["core"]), _dptr(out["round"]), _dptr(out["uf"]),
+        _dptr(out["L"]), LINK_MODES[link_mode], ctypes.byref(st) if st is not None else None, _stream(stream)))
+    res = {k: out[k][: ri.n_r] for k in ("core", "round", "uf", "L")}
+    if st is not None:
+        res["stats"] = st.as_dict()
+    return res
+
+
+def construct_tree(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent: torch.Tensor | None = None,
+                   label: torch.Tensor | None = None, stream=None):
+    n_r = core.numel()
+    if parent is None:
+        parent = torch.empty(max(2 * n_r, 1), dtype=torch.int32, device="cuda")
+    if label is None:
+        label = torch.empty(max(n_r, 1), dtype=torch.int32, device="cuda")
+    nn = I64()
+    _check("nh_construct_tree", lib().nh_construct_tree(n_r, _dptr(core), _dptr(uf), _dptr(L), _dptr(parent),
+                                                        _dptr(label), ctypes.byref(nn), _stream(stream)))
+    return parent[: n_r + nn.value], label[: nn.value], nn.value
+
+
+def approx_nucleus(o: Oriented, ri: RIndex, s: int, delta: float, cnt: torch.Tensor, stats: bool = False,
+                   stream=None) -> dict:
+    n = max(ri.n_r, 1)
+    approx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rnd = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = PeelStats() if stats else None
+    _check("nh_approx_nucleus", lib().nh_approx_nucleus(o.handle, ri.handle, s, float(delta), _dptr(cnt),
+                                                        _dptr(approx), _dptr(rnd),
+                                                        ctypes.byref(st) if st is not None else None,
+                                                        _stream(stream)))
+    res = {"approx": approx[: ri.n_r], "round": rnd[: ri.n_r]}
+    if st is not None:
+        res["stats"] = st.as_dict()
+    return res
+
+
+def link_pairs(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, pairs: torch.Tensor, stream=None):
+    """link-efficient (Alg. 5) on a batch of (R, Q) calls; uf and L are updated in place."""
+    pairs = pairs.to(torch.int32).contiguous()
+    _check("nh_link_pairs", lib().nh_link_pairs(core.numel(), _dptr(core), _dptr(uf), _dptr(L), _dptr(pairs),
+                                                pairs.numel() // 2, _stream(stream)))
+
+
+def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: str = "def", stats: bool = False,
+              stream=None) -> dict:
+    """The whole exact path on device tensors: orientation, r-clique index, s-clique counts, peel
+    with link-efficient, construct-tree."""
+    o = build_orientation(off, adj, stream)
+    ri = index_r_cliques(o, r, stream)
+    cnt, n_s = count_s_cliques(o, ri, s, stream=stream)
+    pk = peel_and_link(o, ri, s, cnt, link_mode=link_mode, stats=stats, stream=stream)
+    parent, label, nn = construct_tree(pk["core"], pk["uf"], pk["L"], stream=stream)
+    res = {"oriented": o, "rindex": ri, "n_r": ri.n_r, "n_s": n_s, "cnt": cnt, "parent": parent,
+           "label": label, "n_nodes": nn}
+    res.update(pk)
+    return res
