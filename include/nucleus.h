@@ -137,6 +137,9 @@ int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double d
 int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L,
                   const int32_t* pairs, int64_t n_pairs, void* stream);
 
+/* number of CUDA kernels this library has launched in the process so far (host counter) */
+int64_t nh_kernel_launches(void);
+
 /* static description of a status code (never NULL) */
 const char* nh_status_string(int status);
 /* library version: major*10000 + minor*100 + patch */

@@ -1,5 +1,13 @@
 // nh_api.cu -- status strings and version of the C-ABI (the entry points live beside their kernels).
+#include <atomic>
+
 #include "nh_internal.cuh"
+
+static std::atomic<long long> g_launches{0};
+
+void nh_note_launch(int64_t k) { g_launches.fetch_add((long long)k, std::memory_order_relaxed); }
+
+extern "C" int64_t nh_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char* nh_status_string(int status) {
   switch (status) {

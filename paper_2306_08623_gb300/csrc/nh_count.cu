@@ -172,13 +172,15 @@ int grid_for(const void* fn, int threads, size_t smem) {
 
 extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
                                   void* stream) {
-  if (!o || !ri || !cnt || ri->o != o) return NH_ERR_INVALID;
+  if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
   if (!nh_supported(r, s) && !(r == 1 && s == 4)) return NH_ERR_UNSUPPORTED;
+  if (!cnt && ri->n_r > 0) return NH_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   GView g = make_view(o, ri);
   if (r == 1 && s == 2) {
     k_count_12<<<nh_blocks_for(o->n, 256, 152 * 32), 256, 0, st>>>(o->n, o->off, cnt);
+    nh_note_launch();
     if (cudaGetLastError() != cudaSuccess) return NH_ERR_CUDA;
     if (n_s) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return NH_ERR_CUDA;
@@ -202,6 +204,7 @@ extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int
     int grid = grid_for(fn, kThreads, 0);
     if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
     else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
+    nh_note_launch();
   } else {
     const int cap = (int)(o->max_out > 0 ? o->max_out : 1);
     const size_t smem = (size_t)kWarpsPerBlock * 3 * cap * sizeof(int32_t);
@@ -217,6 +220,7 @@ extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int
     if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
     else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
     else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
+    nh_note_launch();
   }
   if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
   unsigned long long hcount = 0;

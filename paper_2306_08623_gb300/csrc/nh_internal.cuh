@@ -159,6 +159,9 @@ static inline unsigned nh_blocks_for(int64_t n, int threads, int64_t cap = 1 << 
   return (unsigned)b;
 }
 
+// count one kernel launch made by the library (reported by nh_kernel_launches)
+void nh_note_launch(int64_t k = 1);
+
 // exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
 int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);
 int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);

@@ -249,10 +249,12 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
     int hbad = 0;
     cudaMemsetAsync(maxes, 0, 3 * sizeof(unsigned long long), st);
     k_check_off<<<nh_blocks_for(n + 1, 256, 152 * 16), 256, 0, st>>>(n, nnz, off, bad);
+    nh_note_launch();
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
     if (!rc && !hbad && nnz > 0) {
       k_check_adj<<<nh_blocks_for(n, 256, 152 * 16), 256, 0, st>>>(n, off, adj, bad);
+      nh_note_launch();
       cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
     }
@@ -266,11 +268,13 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
   }
   cudaMemsetAsync(maxes, 0, 3 * sizeof(unsigned long long), st);
   k_orient_count<<<warp_grid(n), kThreads, 0, st>>>(n, off, adj, outdeg, updeg, maxes);
+  nh_note_launch();
   if (!rc) rc = nh_exclusive_scan_u32(outdeg, o->ooff, n, st);
   if (!rc) rc = nh_exclusive_scan_u32(updeg, o->uoff, n, st);
   if (!rc) {
     k_orient_fill<<<warp_grid(n), kThreads, 0, st>>>(n, m, off, adj, o->uoff, o->ooff, o->eid, o->eu, o->ev, o->oadj,
                                                      o->oeid, o->osrc, (int*)(maxes + 2));
+    nh_note_launch();
     cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&m_check, o->uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   }
@@ -320,6 +324,7 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
       return rc;
     }
     k_tri_count<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eu, o->ev, tcount);
+    nh_note_launch();
     rc = nh_exclusive_scan_u32(tcount, ri->toff, m, st);
     int64_t ntri = 0;
     if (!rc) cudaMemcpyAsync(&ntri, ri->toff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -334,8 +339,10 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
       ri->n_r = ntri;
       cudaMemsetAsync(status, 0, sizeof(int), st);
       k_fill_empty<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(ri->table, cap);
+      nh_note_launch();
       k_tri_fill<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eu, o->ev, ri->toff, ri->tri, ri->table,
                                                      ri->mask, status);
+    nh_note_launch();
       int hs = 0;
       cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
@@ -358,6 +365,7 @@ extern "C" int nh_rindex_tuples(const nh_rindex* ri, int32_t* tuples, void* stre
   cudaStream_t st = (cudaStream_t)stream;
   if (ri->n_r == 0) return NH_OK;
   k_tuples<<<nh_blocks_for(ri->n_r, 256, 152 * 32), 256, 0, st>>>(ri->r, ri->n_r, ri->o->eu, ri->o->ev, ri->tri, tuples);
+  nh_note_launch();
   return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 

@@ -226,18 +226,23 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
       if (pQ != Q) push(__ldcg(E.L + Q), pQ);
       continue;
     }
-    // nR < nQ
+    // nR < nQ.  L[Q] is read only after Q is re-found as a root, and the value that was tested is
+    // the one passed on: with concurrent unites, a value read from a component that has just
+    // stopped being a root (or re-read after the test) could drop the fact "R meets Q at level
+    // nR" -- the sequential order of the paper's loop does not survive concurrency otherwise.
     for (unsigned int spin = 0;; ++spin) {
       if (spin > (1u << 20)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
-      const int32_t LQ = __ldcg(E.L + Q);
       Q = uf_find(E.uf, Q);
-      if (atomicCAS(E.L + Q, -1, R) == -1) {
-        __threadfence();
-        const int32_t pQ = uf_find(E.uf, Q);
-        if (pQ != Q) push(R, pQ);
-        break;
+      const int32_t LQ = __ldcg(E.L + Q);
+      if (LQ < 0) {
+        if (atomicCAS(E.L + Q, -1, R) == -1) {
+          __threadfence();
+          const int32_t pQ = uf_find(E.uf, Q);
+          if (pQ != Q) push(R, pQ);
+          break;
+        }
+        continue;  // L[Q] was set meanwhile: retry with its value
       }
-      if (LQ < 0) continue;  // L[Q] was set after our read: retry with the current value
       if (__ldcg(E.core + LQ) < nR) {
         if (atomicCAS(E.L + Q, LQ, R) == LQ) {
           __threadfence();
@@ -248,7 +253,7 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
         }
         continue;
       }
-      push(R, __ldcg(E.L + Q));
+      push(R, LQ);
       break;
     }
   }
@@ -271,9 +276,90 @@ __device__ __forceinline__ void dec(const PeelArgs& A, int32_t x, uint32_t t, ui
   }
 }
 
+__device__ __forceinline__ int32_t tri_id(const PeelArgs& A, unsigned long long key, LocalStats& ls) {
+  ls.probe++;
+  const int64_t id = nh_tri_lookup(A.g.table, A.g.mask, key);
+  if (id < 0) {
+    atomicCAS(&A.lk.ctl->err, 0, NH_ERR_INTERNAL);
+    return 0;
+  }
+  return (int32_t)id;
+}
+
+// ---------------------------------------------------------------------------------------------
+// per-warp link buffer: the link targets of one frontier r-clique R are collected, replaced by
+// their union-find roots, sorted by decreasing core and de-duplicated, then linked as a chain
+// R - t1 - t2 - ... (t_i = targets in that order).  Since R meets t_i at level core(t_i) and
+// core(t_{i-1}) >= core(t_i), "t_{i-1} meets t_i at level core(t_i)" states the same
+// connectivity as "R meets t_i at core(t_i)", while link-efficient walks only between adjacent
+// levels instead of from R's level down to each target's level.
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kLinkBuf = 256;
+
+struct WarpLinks {
+  unsigned long long* buf;
+  int* cnt;
+};
+
+__device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int32_t m,
+                                       LocalStats& ls) {
+  const int pos = atomicAdd(W.cnt, 1);
+  if (pos < kLinkBuf) W.buf[pos] = (unsigned long long)(uint32_t)m;
+  else link_run(A.lk, Rid, m, ls);  // buffer full (cannot happen with the flush policy): link directly
+}
+
+// warp-collective
+__device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane, LocalStats& ls) {
+  __syncwarp();
+  const int n = min(*(volatile int*)W.cnt, kLinkBuf);
+  if (n == 0) return;
+  for (int i = lane; i < kLinkBuf; i += 32) {
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const int32_t rt = uf_find(A.lk.uf, (int32_t)W.buf[i]);
+      const uint32_t c = __ldcg(A.val + rt);
+      key = ((unsigned long long)(~c) << 32) | (uint32_t)rt;
+    }
+    W.buf[i] = key;
+  }
+  __syncwarp();
+  for (int k = 2; k <= kLinkBuf; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < kLinkBuf; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = W.buf[i], b = W.buf[ixj];
+          if ((a > b) == ((i & k) == 0)) {
+            W.buf[i] = b;
+            W.buf[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < n; i += 32) {
+    const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
+    const int32_t prev = (i == 0) ? Rid : (int32_t)(W.buf[i - 1] & 0xffffffffull);
+    if (i > 0 && prev == cur) continue;
+    link_run(A.lk, prev, cur, ls);
+  }
+  __syncwarp();
+  if (lane == 0) *W.cnt = 0;
+  __syncwarp();
+}
+
+// flush when another step of 32 lanes could overflow the buffer (warp-collective)
+__device__ __forceinline__ void wl_maybe_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane,
+                                               int per_lane, LocalStats& ls) {
+  __syncwarp();
+  if (*(volatile int*)W.cnt > kLinkBuf - 32 * per_lane) wl_flush(W, A, Rid, lane, ls);
+}
+
 template <int CM, bool EXACT>
 __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM], uint32_t t,
-                                          uint32_t thr, int32_t* nf, LocalStats& ls) {
+                                          uint32_t thr, int32_t* nf, const WarpLinks& W, LocalStats& ls) {
   uint32_t rd[CM];
   bool dead = false;
   int32_t attr = Rid;
@@ -295,7 +381,7 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
           if (c < bc) { bc = c; best = mem[j]; }
         }
       }
-      link_run(A.lk, Rid, best, ls);
+      wl_add(W, A, Rid, best, ls);
     }
   } else if (attr == Rid) {
 #pragma unroll
@@ -304,24 +390,14 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
     if (EXACT && A.link_mode == 0) {
 #pragma unroll
       for (int j = 0; j < CM; j++)
-        if (rd[j] == t) link_run(A.lk, Rid, mem[j], ls);
+        if (rd[j] == t) wl_add(W, A, Rid, mem[j], ls);
     }
   }
   if (EXACT && A.link_mode == 1) {
 #pragma unroll
     for (int j = 0; j < CM; j++)
-      if (rd[j] != 0u && rd[j] <= t) link_run(A.lk, mem[j], Rid, ls);
+      if (rd[j] != 0u && rd[j] <= t) wl_add(W, A, Rid, mem[j], ls);
   }
-}
-
-__device__ __forceinline__ int32_t tri_id(const PeelArgs& A, unsigned long long key, LocalStats& ls) {
-  ls.probe++;
-  const int64_t id = nh_tri_lookup(A.g.table, A.g.mask, key);
-  if (id < 0) {
-    atomicCAS(&A.lk.ctl->err, 0, NH_ERR_INTERNAL);
-    return 0;
-  }
-  return (int32_t)id;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -330,7 +406,8 @@ __device__ __forceinline__ int32_t tri_id(const PeelArgs& A, unsigned long long 
 
 template <int R, int S, bool EXACT>
 __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
-                            LocalStats& ls) {
+                            const WarpLinks& W, LocalStats& ls) {
+  constexpr int kPerLane = (S - R == 1) ? R : 5;  // link targets one lane can add per converged step
   const GView& g = A.g;
   int32_t vx[3] = {0, 0, 0};
   int32_t eR[3] = {0, 0, 0};  // r = 3: edges (v0,v1), (v0,v2), (v1,v2)
@@ -388,16 +465,16 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
       if (ok) {
         if constexpr (R == 1) {
           const int32_t mem[1] = {w};
-          process_S<1, EXACT>(A, Rid, mem, t, thr, nf, ls);
+          process_S<1, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
         } else if constexpr (R == 2) {
           const int32_t mem[2] = {ew[0], ew[1]};
-          process_S<2, EXACT>(A, Rid, mem, t, thr, nf, ls);
+          process_S<2, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
         } else {
           const int32_t mem[3] = {
               tri_id(A, nh_tri_key(vx[0], vx[1], w, eR[0], ew[0], ew[1]), ls),
               tri_id(A, nh_tri_key(vx[0], vx[2], w, eR[1], ew[0], ew[2]), ls),
               tri_id(A, nh_tri_key(vx[1], vx[2], w, eR[2], ew[1], ew[2]), ls)};
-          process_S<3, EXACT>(A, Rid, mem, t, thr, nf, ls);
+          process_S<3, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
         }
       }
     } else {
@@ -440,16 +517,19 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
           if (okx) {
             if constexpr (R == 1) {
               const int32_t mem[2] = {ow, x};
-              process_S<2, EXACT>(A, Rid, mem, t, thr, nf, ls);
+              process_S<2, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
             } else if constexpr (R == 2) {
               const int32_t mem[5] = {oe0, oe1, ex[0], ex[1], e_wx};
-              process_S<5, EXACT>(A, Rid, mem, t, thr, nf, ls);
+              process_S<5, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
             }
           }
         }
+        if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
       }
     }
+    if constexpr (EXACT && S - R == 1) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
   }
+  if constexpr (EXACT) wl_flush(W, A, Rid, lane, ls);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -527,6 +607,11 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
+  __shared__ int s_lcnt[kThreads / 32];
+  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
+  __syncwarp();
+  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5]};
   for (;;) {
     if (vc->done || vc->err) break;
     if (vc->need_scan) {
@@ -592,7 +677,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
       for (unsigned long long it = (unsigned long long)gwarp; it < fs; it += (unsigned long long)nwarps)
-        relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, ls);
+        relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, W, ls);
     }
     // end of round: drain deferred link calls, then advance
     bool ok = true;
@@ -697,6 +782,7 @@ int launch_peel(PeelArgs& A, cudaStream_t st) {
   dim3 grid((unsigned)(sms * per)), block(kThreads);
   void* args[] = {&A};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st);
+  nh_note_launch();
   return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
 
@@ -714,8 +800,11 @@ int dispatch(int r, int s, PeelArgs& A, cudaStream_t st) {
 int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* val,
              uint32_t* round, int32_t* uf, int32_t* L, int link_mode, double delta, nh_peel_stats* stats,
              cudaStream_t st) {
-  if (!o || !ri || ri->o != o || !cnt || !val || !round) return NH_ERR_INVALID;
+  if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
+  if (stats) *stats = nh_peel_stats{};
+  if (ri->n_r == 0 && nh_supported(r, s)) return NH_OK;  // arrays may be empty (null)
+  if (!cnt || !val || !round) return NH_ERR_INVALID;
   if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
   if (exact && (!uf || !L || link_mode < 0 || link_mode > 1)) return NH_ERR_INVALID;
   if (!exact && !(delta > 0.0)) return NH_ERR_INVALID;
@@ -755,6 +844,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
     if ((rc = nh_alloc(&dmax, 1, st))) goto cleanup;
     cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
     k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, cnt, dmax);
+    nh_note_launch();
     unsigned int hmax = 0;
     cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
@@ -776,8 +866,10 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   }
   cudaMemsetAsync(A.lk.ctl, 0, sizeof(PeelCtl), st);
   k_ctl_init<<<1, 1, 0, st>>>(A.lk.ctl, n_r, exact ? 0u : thr_host[0]);
+  nh_note_launch();
   k_peel_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, cnt, A.cnt, round, val, A.alive[0],
                                                                   exact ? uf : nullptr, exact ? L : nullptr);
+  nh_note_launch();
   if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
   rc = exact ? dispatch<true>(r, s, A, st) : dispatch<false>(r, s, A, st);
   if (!rc) {
@@ -840,6 +932,7 @@ extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int
   cudaMemsetAsync(E.ctl, 0, sizeof(PeelCtl), st);
   k_link_pairs<<<nh_blocks_for(n_pairs, 128, 152 * 16), 128, 0, st>>>(E, (const int2*)pairs,
                                                                     (unsigned long long)n_pairs);
+  nh_note_launch();
   PeelCtl h{};
   for (int iter = 0; iter < 1000 && !rc; iter++) {
     cudaMemcpyAsync(&h, E.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
@@ -847,7 +940,9 @@ extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int
     if (h.err) { rc = h.err; break; }
     if (h.ovf_count[h.ovf_cur] == 0) break;
     k_link_swap<<<1, 1, 0, st>>>(E.ctl, E.ovf_cap);
+    nh_note_launch();
     k_link_drain<<<152 * 8, 128, 0, st>>>(E);
+    nh_note_launch();
   }
   nh_free(E.ctl, st); nh_free(E.ovf[0], st); nh_free(E.ovf[1], st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;

@@ -70,12 +70,16 @@ extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf,
   cudaMemsetAsync(own, 0, sizeof(uint32_t) * n_r, st);
   cudaMemsetAsync(nch, 0, sizeof(uint32_t) * n_r, st);
   k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own);
+  nh_note_launch();
   k_tree_children<<<blocks, 256, 0, st>>>(n_r, uf, L, nch);
+  nh_note_launch();
   k_tree_flags<<<blocks, 256, 0, st>>>(n_r, uf, own, nch, flag);
+  nh_note_launch();
   rc = nh_exclusive_scan_u32(flag, nid, n_r, st);
   int64_t nn = 0;
   if (!rc) {
     k_tree_write<<<blocks, 256, 0, st>>>(n_r, uf, L, core, flag, nid, parent, label);
+    nh_note_launch();
     cudaMemcpyAsync(&nn, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   }
   if (cudaGetLastError() != cudaSuccess && !rc) rc = NH_ERR_CUDA;

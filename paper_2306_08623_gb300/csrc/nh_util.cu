@@ -100,8 +100,11 @@ int scan_impl(const T* in, int64_t* out, int64_t n, cudaStream_t st) {
   int rc = nh_alloc(&bsum, nb, st);
   if (rc) return rc;
   k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum);
+  nh_note_launch();
   k_scan_bsums<<<1, kScanThreads, 0, st>>>(bsum, nb, out + n);
+  nh_note_launch();
   k_scan_final<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum, out);
+  nh_note_launch();
   cudaError_t e = cudaGetLastError();
   nh_free(bsum, st);
   return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;

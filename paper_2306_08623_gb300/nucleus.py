@@ -63,6 +63,7 @@ def lib():
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
             "nh_version": (I32, []),
+            "nh_kernel_launches": (I64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -199,6 +200,11 @@ def link_pairs(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, pairs: tor
     pairs = pairs.to(torch.int32).contiguous()
     _check("nh_link_pairs", lib().nh_link_pairs(core.numel(), _dptr(core), _dptr(uf), _dptr(L), _dptr(pairs),
                                                 pairs.numel() // 2, _stream(stream)))
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by the library in this process so far."""
+    return int(lib().nh_kernel_launches())
 
 
 def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: str = "def", stats: bool = False,
