@@ -9,6 +9,8 @@
 //   eu[m], ev[m]    endpoints of edge id e (eu < ev)
 //   tri[3 n_r]      vertices of triangle id t (r = 3), toff[m+1] (i64) first triangle id per edge
 //   table[cap]      16-byte slots {key u64, id u32, pad}: key = (edge id of (a,b)) << 32 | c
+//   etoff[m+1] (i64), etw[3 n_r], ettid[3 n_r]   r = 3: for every edge (p,q), the third vertices w
+//                   of all triangles {p,q,w} in ascending order, with the triangle ids
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,6 +51,9 @@ struct nh_rindex {
   int64_t* toff;
   nh_slot* table;
   unsigned long long mask;
+  int64_t* etoff;
+  int32_t* etw;
+  int32_t* ettid;
   cudaStream_t stream;
 };
 
@@ -66,6 +71,9 @@ struct GView {
   const int32_t* tri;
   const nh_slot* table;
   unsigned long long mask;
+  const int64_t* etoff;
+  const int32_t* etw;
+  const int32_t* ettid;
   int64_t n, m;
 };
 
@@ -77,6 +85,9 @@ static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
   g.tri = ri ? ri->tri : nullptr;
   g.table = ri ? ri->table : nullptr;
   g.mask = ri ? ri->mask : 0ull;
+  g.etoff = ri ? ri->etoff : nullptr;
+  g.etw = ri ? ri->etw : nullptr;
+  g.ettid = ri ? ri->ettid : nullptr;
   g.n = o->n; g.m = o->m;
   return g;
 }

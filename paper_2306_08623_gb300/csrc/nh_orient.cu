@@ -179,6 +179,68 @@ __global__ void k_tri_fill(int64_t m, const int64_t* __restrict__ off, const int
   }
 }
 
+// all triangles per edge (a,b): |N(a) n N(b)|
+__global__ void k_et_count(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                           uint32_t* __restrict__ etcount) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int32_t a = eu[e], b = ev[e];
+    int64_t sb = off[a], se = off[a + 1], lb = off[b], le = off[b + 1];
+    if (se - sb > le - lb) {
+      int64_t t0 = sb, t1 = se;
+      sb = lb; se = le; lb = t0; le = t1;
+    }
+    uint32_t cnt = 0;
+    for (int64_t j = sb + lane; j < se; j += 32) cnt += (nh_find(adj, lb, le, adj[j]) >= 0) ? 1u : 0u;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(NH_FULL, cnt, d);
+    if (lane == 0) etcount[e] = cnt;
+  }
+}
+
+// per edge (a,b): the third vertices w of its triangles, ascending, and each triangle's id
+__global__ void k_et_fill(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                          const int32_t* __restrict__ eid, const int32_t* __restrict__ eu,
+                          const int32_t* __restrict__ ev, const int64_t* __restrict__ etoff,
+                          const nh_slot* __restrict__ table, unsigned long long mask, int32_t* __restrict__ etw,
+                          int32_t* __restrict__ ettid, int* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int32_t a = eu[e], b = ev[e];
+    int64_t sb = off[a], se = off[a + 1], lb = off[b], le = off[b + 1];
+    const bool scan_a = (se - sb) <= (le - lb);
+    if (!scan_a) {
+      int64_t t0 = sb, t1 = se;
+      sb = lb; se = le; lb = t0; le = t1;
+    }
+    int64_t pos = etoff[e];
+    for (int64_t base = sb; base < se; base += 32) {
+      const int64_t j = base + lane;
+      int32_t w = 0;
+      int64_t q = -1;
+      if (j < se) {
+        w = adj[j];
+        q = nh_find(adj, lb, le, w);
+      }
+      const unsigned msk = __ballot_sync(NH_FULL, q >= 0);
+      if (q >= 0) {
+        const int64_t k = pos + __popc(msk & ((1u << lane) - 1u));
+        const int32_t e_aw = eid[scan_a ? j : q], e_bw = eid[scan_a ? q : j];
+        const int64_t id = nh_tri_lookup(table, mask, nh_tri_key(a, b, w, (int32_t)e, e_aw, e_bw));
+        if (id < 0) atomicExch(status, NH_ERR_INTERNAL);
+        etw[k] = w;
+        ettid[k] = (int32_t)id;
+      }
+      pos += __popc(msk);
+    }
+  }
+}
+
 __global__ void k_fill_empty(nh_slot* t, unsigned long long cap) {
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -214,6 +276,7 @@ void free_oriented(nh_oriented* o) {
 void free_rindex(nh_rindex* ri) {
   if (!ri) return;
   cudaFree(ri->tri); cudaFree(ri->toff); cudaFree(ri->table);
+  cudaFree(ri->etoff); cudaFree(ri->etw); cudaFree(ri->ettid);
   delete ri;
 }
 
@@ -347,6 +410,28 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
       cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
       if (!rc && hs) rc = hs;
+    }
+    // per-edge triangle lists (every triangle appears in the lists of its three edges)
+    if (!rc) rc = nh_alloc(&ri->etoff, m + 1, st);
+    if (!rc) {
+      k_et_count<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eu, o->ev, tcount);
+      nh_note_launch();
+      rc = nh_exclusive_scan_u32(tcount, ri->etoff, m, st);
+    }
+    if (!rc) rc = nh_alloc(&ri->etw, 3 * ntri, st);
+    if (!rc) rc = nh_alloc(&ri->ettid, 3 * ntri, st);
+    if (!rc) {
+      cudaMemsetAsync(status, 0, sizeof(int), st);
+      k_et_fill<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eid, o->eu, o->ev, ri->etoff, ri->table,
+                                                    ri->mask, ri->etw, ri->ettid, status);
+      nh_note_launch();
+      int hs = 0;
+      int64_t tot = -1;
+      cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&tot, ri->etoff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
+      if (!rc && hs) rc = hs;
+      if (!rc && tot != 3 * ntri) rc = NH_ERR_INTERNAL;
     }
     nh_free(tcount, st); nh_free(status, st);
     if (rc) {

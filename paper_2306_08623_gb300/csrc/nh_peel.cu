@@ -406,7 +406,7 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 
 template <int R, int S, bool EXACT>
 __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
-                            const WarpLinks& W, LocalStats& ls) {
+                            int sub, int G, const WarpLinks& W, LocalStats& ls) {
   constexpr int kPerLane = (S - R == 1) ? R : 5;  // link targets one lane can add per converged step
   const GView& g = A.g;
   int32_t vx[3] = {0, 0, 0};
@@ -431,6 +431,42 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
     eR[1] = __shfl_sync(NH_FULL, mine, 1);
     eR[2] = __shfl_sync(NH_FULL, mine, 2);
   }
+  if constexpr (R == 3 && S == 4) {
+    // the 4-cliques on triangle R = {v0,v1,v2} are the w common to the triangle lists of its
+    // three edges; the ids of {v0,v1,w}, {v0,v2,w}, {v1,v2,w} are read from the list positions
+    int64_t tl[3], th[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      tl[i] = __ldg(g.etoff + eR[i]);
+      th[i] = __ldg(g.etoff + eR[i] + 1);
+    }
+    int bt = 0;
+    if (th[1] - tl[1] < th[bt] - tl[bt]) bt = 1;
+    if (th[2] - tl[2] < th[bt] - tl[bt]) bt = 2;
+    if (lane == 0 && sub == 0) ls.scan += (unsigned long long)(th[bt] - tl[bt]);
+    for (int64_t base = tl[bt] + 32 * sub; base < th[bt]; base += 32 * G) {
+      const int64_t j = base + lane;
+      bool ok = j < th[bt];
+      int32_t mem[3] = {0, 0, 0};
+      if (ok) {
+        const int32_t w = __ldg(g.etw + j);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+          if (i == bt) {
+            mem[i] = __ldg(g.ettid + j);
+          } else if (ok) {
+            const int64_t p = nh_find(g.etw, tl[i], th[i], w);
+            if (p < 0) ok = false;
+            else mem[i] = __ldg(g.ettid + p);
+          }
+        }
+      }
+      if (ok) process_S<3, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
+      if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
+    }
+    if constexpr (EXACT) wl_flush(W, A, Rid, lane, ls);
+    return;
+  }
   int64_t lo[3], hi[3];
 #pragma unroll
   for (int i = 0; i < R; i++) {
@@ -442,8 +478,8 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
   for (int i = 1; i < R; i++)
     if (hi[i] - lo[i] < hi[best] - lo[best]) best = i;
   const int64_t b0 = lo[best], b1 = hi[best];
-  if (lane == 0) ls.scan += (unsigned long long)(b1 - b0);
-  for (int64_t base = b0; base < b1; base += 32) {
+  if (lane == 0 && sub == 0) ls.scan += (unsigned long long)(b1 - b0);
+  for (int64_t base = b0 + 32 * sub; base < b1; base += 32 * G) {
     const int64_t j = base + lane;
     bool ok = j < b1;
     int32_t w = 0;
@@ -676,8 +712,17 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
       const unsigned long long fs = vc->fsize;
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
-      for (unsigned long long it = (unsigned long long)gwarp; it < fs; it += (unsigned long long)nwarps)
-        relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, W, ls);
+      // a small frontier gets several warps per r-clique (G, a power of two up to 64); the
+      // warps of a group take interleaved 32-entry chunks of the scanned list
+      int G = 1;
+      while (G < 64 && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
+      const long long ngroups = nwarps / G;
+      const long long grp = gwarp / G;
+      const int sub = (int)(gwarp % G);
+      if (grp < ngroups) {
+        for (unsigned long long it = (unsigned long long)grp; it < fs; it += (unsigned long long)ngroups)
+          relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, sub, G, W, ls);
+      }
     }
     // end of round: drain deferred link calls, then advance
     bool ok = true;
