@@ -65,6 +65,8 @@ struct LinkEnv {
   int32_t* uf;
   int32_t* L;
   const uint32_t* core;
+  unsigned long long* cache;        // lossy set of linked root pairs (may be null)
+  unsigned long long cache_mask;
   int2* ovf[2];
   unsigned long long ovf_cap;
   PeelCtl* ctl;
@@ -169,20 +171,22 @@ __device__ __forceinline__ int32_t uf_find(int32_t* uf, int32_t x) {
   return x;
 }
 
-// unite the sets of a and b: the root of larger id is hung under the root of smaller id
-__device__ __forceinline__ bool uf_unite(int32_t* uf, int32_t a, int32_t b, PeelCtl* ctl) {
+// unite the sets of a and b: the root of larger id is hung under the root of smaller id.
+// Returns the root that was hung (it is this caller's job to pass on its L entry), or -1 when
+// a and b were already in one set.
+__device__ __forceinline__ int32_t uf_unite(int32_t* uf, int32_t a, int32_t b, PeelCtl* ctl) {
   for (int it = 0; it < (1 << 20); ++it) {
     a = uf_find(uf, a);
     b = uf_find(uf, b);
-    if (a == b) return false;
+    if (a == b) return -1;
     if (a < b) { const int32_t t = a; a = b; b = t; }
     if (atomicCAS(uf + a, a, b) == a) {
       __threadfence();
-      return true;
+      return a;
     }
   }
   atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
-  return false;
+  return -1;
 }
 
 __device__ __forceinline__ void ovf_push(const LinkEnv& E, int32_t a, int32_t b, LocalStats& ls) {
@@ -218,12 +222,24 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
     }
     R = uf_find(E.uf, R);
     Q = uf_find(E.uf, Q);
+    if (R == Q) continue;
+    if (E.cache) {
+      // a pair of roots already linked states nothing new (components only grow)
+      const unsigned long long key = ((unsigned long long)(uint32_t)R << 32) | (uint32_t)Q;
+      unsigned long long* slot = E.cache + (nh_mix64(key) & E.cache_mask);
+      if (__ldcg(slot) == key) continue;
+      *slot = key;
+    }
     if (nR == nQ) {
-      if (R != Q && uf_unite(E.uf, R, Q, E.ctl)) ls.unite++;
-      const int32_t pR = uf_find(E.uf, R);
-      if (pR != R) push(__ldcg(E.L + R), pR);
-      const int32_t pQ = uf_find(E.uf, Q);
-      if (pQ != Q) push(__ldcg(E.L + Q), pQ);
+      // Alg. 5 passes on L of whichever of R, Q stopped being a root.  Concurrently the roots
+      // actually joined may be others (R or Q may have been hung meanwhile), so the thread whose
+      // CAS hung a root passes on that root's L -- every hung root is handled exactly by the
+      // thread that hung it.
+      const int32_t child = uf_unite(E.uf, R, Q, E.ctl);
+      if (child >= 0) {
+        ls.unite++;
+        push(__ldcg(E.L + child), uf_find(E.uf, child));
+      }
       continue;
     }
     // nR < nQ.  L[Q] is read only after Q is re-found as a root, and the value that was tested is
@@ -882,6 +898,11 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   if (exact) {
     if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
       goto cleanup;
+    unsigned long long cap = 4096;
+    while (cap < 2ull * (unsigned long long)n_r && cap < (1ull << 24)) cap <<= 1;
+    if ((rc = nh_alloc(&A.lk.cache, (int64_t)cap, st))) goto cleanup;
+    A.lk.cache_mask = cap - 1;
+    cudaMemsetAsync(A.lk.cache, 0xff, sizeof(unsigned long long) * cap, st);
   }
   if (!exact) {
     // bucket upper ends t_i = floor(x_i), x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta), up to
@@ -940,6 +961,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
 cleanup:
   nh_free(A.cnt, st); nh_free(A.alive[0], st); nh_free(A.alive[1], st); nh_free(A.front[0], st);
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
+  nh_free(A.lk.cache, st);
   nh_free(thr_dev, st); nh_free(dmax, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
