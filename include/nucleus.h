@@ -137,6 +137,35 @@ int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double d
 int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L,
                   const int32_t* pairs, int64_t n_pairs, void* stream);
 
+/* a11 -- learned work estimator for the s-clique listing (rec-list-cliques) work.
+ * Work items are the out-edges (v -> a) of the orientation in CSR order; a partition gives each
+ * warp of the counting kernel one contiguous item range of equal estimated cost.  Counts do not
+ * depend on the partition.  The estimator is an MLP NH_MLP_FEATURES -> 64 -> 64 -> 1 (ReLU),
+ * BF16 weights, FP32 accumulation, trained (Adam, full batch, MSE on log1p(cost)) on the
+ * per-vertex costs that the counting kernel itself measures.  The paper has no counterpart: it
+ * schedules this work with a work-stealing scheduler (§3).
+ * Weight layout (bf16, NH_MLP_PARAMS entries): W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define NH_MLP_FEATURES 8
+#define NH_MLP_HIDDEN 64
+#define NH_MLP_PARAMS 4801
+/* feats float[n * NH_MLP_FEATURES]: log1p of degree, out-degree, 2-hop out-degree sum, 2-hop
+ * degree sum, largest out-neighbour out-degree, sum of min out-degrees; (log out-degree)^2 / 8; 1 */
+int nh_vertex_features(const nh_oriented* o, float* feats, void* stream);
+/* cost float[n]: measured listing work per vertex (list entries touched incl. binary-search
+ * steps) of one counting pass for (r,s); NH_ERR_UNSUPPORTED for (1,2) */
+int nh_listing_cost(const nh_oriented* o, const nh_rindex* ri, int s, float* cost, void* stream);
+/* cost float[n] = d+(v)^(s-1): the degree-based baseline estimate */
+int nh_degree_cost(const nh_oriented* o, int s, float* cost, void* stream);
+/* train on n_train vertices sampled (counter-based hash of seed) from feats/cost (n rows);
+ * weights uint16[NH_MLP_PARAMS] (bf16 bit patterns, written); *final_loss (host, may be NULL) */
+int nh_mlp_train(const float* feats, const float* cost, int64_t n, int64_t n_train, int steps, float lr,
+                 uint64_t seed, uint16_t* weights, float* final_loss, void* stream);
+/* pred float[n] = predicted listing cost per vertex */
+int nh_mlp_predict(const float* feats, int64_t n, const uint16_t* weights, float* pred, void* stream);
+/* nh_count_s_cliques with the items split by vertex_cost (float[n], any estimate) */
+int nh_count_s_cliques_partitioned(const nh_oriented* o, const nh_rindex* ri, int s, const float* vertex_cost,
+                                   uint32_t* cnt, uint64_t* n_s, void* stream);
+
 /* number of CUDA kernels this library has launched in the process so far (host counter) */
 int64_t nh_kernel_launches(void);
 

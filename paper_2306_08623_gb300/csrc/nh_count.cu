@@ -28,13 +28,22 @@ __global__ void k_count_12(int64_t n, const int64_t* __restrict__ off, uint32_t*
 }
 
 // s = 3: triangles (v, a, b) with a, b in N+(v), b in N+(a)
+// Work items are out-edges (v -> a).  With bounds == null the warps stride over all items;
+// otherwise warp w takes the contiguous item range [bounds[w], bounds[w+1]).  When cost != null
+// the work of each item (list entries touched, binary-search steps included) is added to
+// cost[v]: the measured listing cost the work estimator learns.
+__device__ __forceinline__ float log2p1(int64_t x) { return log2f((float)x + 1.0f); }
+
 template <int R>
-__global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s) {
+__global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
+                           const int64_t* __restrict__ bounds, float* __restrict__ cost) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long found = 0;
-  for (int64_t p = warp; p < g.m; p += nwarps) {
+  const int64_t p0 = bounds ? bounds[warp] : warp, p1 = bounds ? bounds[warp + 1] : g.m;
+  const int64_t pst = bounds ? 1 : nwarps;
+  for (int64_t p = p0; p < p1; p += pst) {
     const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
     int64_t sb = g.ooff[v], se = g.ooff[v + 1];  // scanned list
     int64_t lb = g.ooff[a], le = g.ooff[a + 1];  // searched list
@@ -59,6 +68,7 @@ __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long lo
       if (R == 2) atomicAdd(&cnt[e_va], tot);
       found += tot;
     }
+    if (cost && lane == 0) atomicAdd(&cost[v], (float)(se - sb) * (1.0f + log2p1(le - lb)) + 1.0f);
   }
   if (lane == 0 && found) atomicAdd(n_s, found);
 }
@@ -67,7 +77,8 @@ __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long lo
 // fits, else in a global per-warp slice); c runs over N+(b) and is searched in C2.
 template <int R>
 __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
-                           int32_t* __restrict__ gscratch, int cap, int use_smem, int* __restrict__ status) {
+                           int32_t* __restrict__ gscratch, int cap, int use_smem, int* __restrict__ status,
+                           const int64_t* __restrict__ bounds, float* __restrict__ cost) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -78,7 +89,9 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
   int32_t* c2e1 = base + cap;  // edge (v, b)
   int32_t* c2e2 = base + 2 * cap;  // edge (a, b)
   unsigned long long found = 0;
-  for (int64_t p = warp; p < g.m; p += nwarps) {
+  const int64_t p0 = bounds ? bounds[warp] : warp, p1 = bounds ? bounds[warp + 1] : g.m;
+  const int64_t pst = bounds ? 1 : nwarps;
+  for (int64_t p = p0; p < p1; p += pst) {
     const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
     int64_t sb = g.ooff[v], se = g.ooff[v + 1];
     int64_t lb = g.ooff[a], le = g.ooff[a + 1];
@@ -87,6 +100,7 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
       int64_t t0 = sb, t1 = se;
       sb = lb; se = le; lb = t0; le = t1;
     }
+    float work = (float)(se - sb) * (1.0f + log2p1(le - lb)) + 1.0f;
     int n2 = 0;
     for (int64_t base_j = sb; base_j < se; base_j += 32) {
       const int64_t j = base_j + lane;
@@ -110,26 +124,17 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
     for (int i = 0; i < n2; i++) {
       const int32_t b = c2v[i], e_vb = c2e1[i], e_ab = c2e2[i];
       const int64_t bb = g.ooff[b], be = g.ooff[b + 1];
+      work += (float)(be - bb) * (1.0f + log2p1(n2));
       uint32_t n3 = 0;
       for (int64_t j = bb + lane; j < be; j += 32) {
         const int32_t c = g.oadj[j];
-        // binary search c in c2v[i+1 .. n2): c must follow b in C2 (sorted) since both are
-        // out-neighbours of v and ids are sorted; search the whole tail
-        int lo = i + 1, hi = n2;
+        // c is an out-neighbour of v and a exactly when it is in C2 (sorted by id)
+        int lo = 0, hi = n2;
         while (lo < hi) {
-          int mid = (lo + hi) >> 1;
+          const int mid = (lo + hi) >> 1;
           if (c2v[mid] < c) lo = mid + 1; else hi = mid;
         }
-        int k = (lo < n2 && c2v[lo] == c) ? lo : -1;
-        if (k < 0) {
-          // c may precede b in id order; search the head as well
-          lo = 0; hi = i;
-          while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (c2v[mid] < c) lo = mid + 1; else hi = mid;
-          }
-          k = (lo < i && c2v[lo] == c) ? lo : -1;
-        }
+        const int k = (lo < n2 && c2v[lo] == c) ? lo : -1;
         if (k < 0) continue;
         n3++;
         const int32_t e_vc = c2e1[k], e_ac = c2e2[k], e_bc = g.oeid[j];
@@ -154,6 +159,7 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
       if (R == 2) atomicAdd(&cnt[e_va], tot_item);
       found += tot_item;
     }
+    if (cost && lane == 0) atomicAdd(&cost[v], work);
     __syncwarp();
   }
   if (lane == 0 && found) atomicAdd(n_s, found);
@@ -170,13 +176,12 @@ int grid_for(const void* fn, int threads, size_t smem) {
 
 }  // namespace
 
-extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
-                                  void* stream) {
+int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
+                  const float* vertex_cost, float* measure, cudaStream_t st) {
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
   if (!nh_supported(r, s) && !(r == 1 && s == 4)) return NH_ERR_UNSUPPORTED;
   if (!cnt && ri->n_r > 0) return NH_ERR_INVALID;
-  cudaStream_t st = (cudaStream_t)stream;
   GView g = make_view(o, ri);
   if (r == 1 && s == 2) {
     k_count_12<<<nh_blocks_for(o->n, 256, 152 * 32), 256, 0, st>>>(o->n, o->off, cnt);
@@ -191,19 +196,25 @@ extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int
   unsigned long long* dcount = nullptr;
   int* status = nullptr;
   int32_t* scratch = nullptr;
+  int64_t* bounds = nullptr;
   int rc = NH_OK;
   if ((rc = nh_alloc(&dcount, 1, st)) || (rc = nh_alloc(&status, 1, st))) {
     nh_free(dcount, st); nh_free(status, st);
     return rc;
   }
+  if (measure) cudaMemsetAsync(measure, 0, sizeof(float) * (size_t)o->n, st);
   cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(status, 0, sizeof(int), st);
   cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ri->n_r, st);
   if (s == 3) {
     const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
     int grid = grid_for(fn, kThreads, 0);
-    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
-    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount);
+    if (vertex_cost && (rc = nh_partition_items(o, vertex_cost, (int64_t)grid * kWarpsPerBlock, &bounds, st))) {
+      nh_free(dcount, st); nh_free(status, st);
+      return rc;
+    }
+    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, bounds, measure);
+    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, bounds, measure);
     nh_note_launch();
   } else {
     const int cap = (int)(o->max_out > 0 ? o->max_out : 1);
@@ -217,9 +228,13 @@ extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int
       return rc;
     }
     const size_t dyn = use_smem ? smem : 0;
-    if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
-    else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
-    else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status);
+    if (vertex_cost && (rc = nh_partition_items(o, vertex_cost, (int64_t)grid * kWarpsPerBlock, &bounds, st))) {
+      nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st);
+      return rc;
+    }
+    if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
+    else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
+    else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
     nh_note_launch();
   }
   if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
@@ -227,9 +242,14 @@ extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int
   int hs = 0;
   cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st);
+  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st); nh_free(bounds, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (!rc && hs) rc = hs;
   if (!rc && n_s) *n_s = hcount;
   return rc;
+}
+
+extern "C" int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
+                                  void* stream) {
+  return nh_count_impl(o, ri, s, cnt, n_s, nullptr, nullptr, (cudaStream_t)stream);
 }

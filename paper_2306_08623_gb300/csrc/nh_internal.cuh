@@ -9,6 +9,7 @@
 //   eu[m], ev[m]    endpoints of edge id e (eu < ev)
 //   tri[3 n_r]      vertices of triangle id t (r = 3), toff[m+1] (i64) first triangle id per edge
 //   table[cap]      16-byte slots {key u64, id u32, pad}: key = (edge id of (a,b)) << 32 | c
+//   ehash[cap]      16-byte slots keyed by (u << 32 | v), u < v, holding the edge id (load <= 0.5)
 //   etoff[m+1] (i64), etw[3 n_r], ettid[3 n_r]   r = 3: for every edge (p,q), the third vertices w
 //                   of all triangles {p,q,w} in ascending order, with the triangle ids
 #pragma once
@@ -40,6 +41,8 @@ struct nh_oriented {
   int32_t* eu;
   int32_t* ev;
   int64_t max_out, max_deg;
+  nh_slot* ehash;
+  unsigned long long emask;
   cudaStream_t stream;  // stream the handle was built on (frees are ordered on it)
 };
 
@@ -68,6 +71,8 @@ struct GView {
   const int32_t* osrc;
   const int32_t* eu;
   const int32_t* ev;
+  const nh_slot* ehash;
+  unsigned long long emask;
   const int32_t* tri;
   const nh_slot* table;
   unsigned long long mask;
@@ -82,6 +87,7 @@ static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
   g.off = o->off; g.adj = o->adj; g.eid = o->eid;
   g.ooff = o->ooff; g.oadj = o->oadj; g.oeid = o->oeid; g.osrc = o->osrc;
   g.eu = o->eu; g.ev = o->ev;
+  g.ehash = o->ehash; g.emask = o->emask;
   g.tri = ri ? ri->tri : nullptr;
   g.table = ri ? ri->table : nullptr;
   g.mask = ri ? ri->mask : 0ull;
@@ -144,6 +150,13 @@ __device__ __forceinline__ int64_t nh_tri_lookup(const nh_slot* __restrict__ t, 
   return -1;
 }
 
+// id of edge {x, y} or -1 when x and y are not adjacent
+__device__ __forceinline__ int64_t nh_edge_id(const GView& g, int32_t x, int32_t y) {
+  const unsigned long long key = (x < y) ? (((unsigned long long)(uint32_t)x << 32) | (uint32_t)y)
+                                         : (((unsigned long long)(uint32_t)y << 32) | (uint32_t)x);
+  return nh_tri_lookup(g.ehash, g.emask, key);
+}
+
 __device__ __forceinline__ unsigned long long nh_globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -172,6 +185,14 @@ static inline unsigned nh_blocks_for(int64_t n, int threads, int64_t cap = 1 << 
 
 // count one kernel launch made by the library (reported by nh_kernel_launches)
 void nh_note_launch(int64_t k = 1);
+
+// counting driver shared by the plain and the partitioned entry points (nh_count.cu); vertex_cost
+// (optional) selects the cost-balanced partition, measure (optional) receives per-vertex cost
+int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
+                  const float* vertex_cost, float* measure, cudaStream_t st);
+// contiguous out-edge item ranges of equal total cost (nh_mlp.cu); *bounds has parts + 1 entries
+int nh_partition_items(const nh_oriented* o, const float* vertex_cost, int64_t parts, int64_t** bounds,
+                       cudaStream_t st);
 
 // exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
 int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);

@@ -241,6 +241,25 @@ __global__ void k_et_fill(int64_t m, const int64_t* __restrict__ off, const int3
   }
 }
 
+__global__ void k_edge_insert(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                              nh_slot* __restrict__ table, unsigned long long mask, int* __restrict__ status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = ((unsigned long long)(uint32_t)eu[e] << 32) | (uint32_t)ev[e];
+    unsigned long long h = nh_mix64(key) & mask;
+    bool done = false;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+      const unsigned long long old = atomicCAS(&table[h].key, NH_EMPTY_KEY, key);
+      if (old == NH_EMPTY_KEY || old == key) {
+        table[h].val = (uint32_t)e;
+        done = true;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    if (!done) atomicExch(status, NH_ERR_TABLE_FULL);
+  }
+}
+
 __global__ void k_fill_empty(nh_slot* t, unsigned long long cap) {
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -269,7 +288,7 @@ unsigned warp_grid(int64_t items) {
 void free_oriented(nh_oriented* o) {
   if (!o) return;
   cudaFree(o->eid); cudaFree(o->ooff); cudaFree(o->oadj); cudaFree(o->oeid); cudaFree(o->osrc);
-  cudaFree(o->uoff); cudaFree(o->eu); cudaFree(o->ev);
+  cudaFree(o->uoff); cudaFree(o->eu); cudaFree(o->ev); cudaFree(o->ehash);
   delete o;
 }
 
@@ -352,6 +371,33 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
   }
   o->max_out = (int64_t)hmax[0];
   o->max_deg = (int64_t)hmax[1];
+  // edge table: (u, v) -> edge id, for one-probe adjacency tests
+  {
+    unsigned long long cap = 1024;
+    while (cap < 2ull * (unsigned long long)m) cap <<= 1;
+    int* status = nullptr;
+    if ((rc = nh_alloc(&o->ehash, (int64_t)cap, st)) || (rc = nh_alloc(&status, 1, st))) {
+      nh_free(status, st);
+      cudaStreamSynchronize(st);
+      free_oriented(o);
+      return rc;
+    }
+    o->emask = cap - 1;
+    cudaMemsetAsync(status, 0, sizeof(int), st);
+    k_fill_empty<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(o->ehash, cap);
+    nh_note_launch();
+    k_edge_insert<<<nh_blocks_for(m, 256, 152 * 32), 256, 0, st>>>(m, o->eu, o->ev, o->ehash, o->emask, status);
+    nh_note_launch();
+    int hs = 0;
+    cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    nh_free(status, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
+    if (!rc && hs) rc = hs;
+    if (rc) {
+      free_oriented(o);
+      return rc;
+    }
+  }
   *out = o;
   return NH_OK;
 }

@@ -507,9 +507,9 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
         if (i == best) {
           ew[i] = __ldg(g.eid + j);
         } else if (ok) {
-          const int64_t p = nh_find(g.adj, lo[i], hi[i], w);
-          if (p < 0) ok = false;
-          else ew[i] = __ldg(g.eid + p);
+          const int64_t id = nh_edge_id(g, vx[i], w);  // one probe instead of a binary search
+          if (id < 0) ok = false;
+          else ew[i] = (int32_t)id;
         }
       }
     }
@@ -562,9 +562,9 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
 #pragma unroll
           for (int i = 0; i < R; i++) {
             if (!okx) break;
-            const int64_t p = nh_find(g.adj, lo[i], hi[i], x);
-            if (p < 0) okx = false;
-            else ex[i] = __ldg(g.eid + p);
+            const int64_t id = nh_edge_id(g, vx[i], x);
+            if (id < 0) okx = false;
+            else ex[i] = (int32_t)id;
           }
           if (okx) {
             if constexpr (R == 1) {

@@ -64,6 +64,13 @@ def lib():
             "nh_status_string": (ctypes.c_char_p, [I32]),
             "nh_version": (I32, []),
             "nh_kernel_launches": (I64, []),
+            "nh_vertex_features": (I32, [P, P, P]),
+            "nh_listing_cost": (I32, [P, P, I32, P, P]),
+            "nh_degree_cost": (I32, [P, I32, P, P]),
+            "nh_mlp_train": (I32, [P, P, I64, I64, I32, ctypes.c_float, ctypes.c_uint64, P,
+                                   ctypes.POINTER(ctypes.c_float), P]),
+            "nh_mlp_predict": (I32, [P, I64, P, P, P]),
+            "nh_count_s_cliques_partitioned": (I32, [P, P, I32, P, P, ctypes.POINTER(ctypes.c_uint64), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -200,6 +207,58 @@ def link_pairs(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, pairs: tor
     pairs = pairs.to(torch.int32).contiguous()
     _check("nh_link_pairs", lib().nh_link_pairs(core.numel(), _dptr(core), _dptr(uf), _dptr(L), _dptr(pairs),
                                                 pairs.numel() // 2, _stream(stream)))
+
+
+MLP_FEATURES = 8
+MLP_PARAMS = 4801
+
+
+def vertex_features(o: Oriented, stream=None) -> torch.Tensor:
+    """(n, 8) float32 work-estimator features per vertex."""
+    f = torch.empty((max(o.n, 1), MLP_FEATURES), dtype=torch.float32, device="cuda")
+    _check("nh_vertex_features", lib().nh_vertex_features(o.handle, _dptr(f), _stream(stream)))
+    return f[: o.n]
+
+
+def listing_cost(o: Oriented, ri: RIndex, s: int, stream=None) -> torch.Tensor:
+    """Measured listing work per vertex of one counting pass (the estimator's training label)."""
+    c = torch.empty(max(o.n, 1), dtype=torch.float32, device="cuda")
+    _check("nh_listing_cost", lib().nh_listing_cost(o.handle, ri.handle, s, _dptr(c), _stream(stream)))
+    return c[: o.n]
+
+
+def degree_cost(o: Oriented, s: int, stream=None) -> torch.Tensor:
+    c = torch.empty(max(o.n, 1), dtype=torch.float32, device="cuda")
+    _check("nh_degree_cost", lib().nh_degree_cost(o.handle, s, _dptr(c), _stream(stream)))
+    return c[: o.n]
+
+
+def mlp_train(feats: torch.Tensor, cost: torch.Tensor, n_train: int = 16384, steps: int = 200, lr: float = 1e-2,
+              seed: int = 1, stream=None):
+    """Train the work estimator; returns (bf16 weights as an int16 tensor, final MSE on log1p cost)."""
+    w = torch.empty(MLP_PARAMS, dtype=torch.int16, device="cuda")
+    loss = ctypes.c_float()
+    _check("nh_mlp_train", lib().nh_mlp_train(_dptr(feats.contiguous()), _dptr(cost.contiguous()), feats.shape[0],
+                                              n_train, steps, float(lr), seed, _dptr(w), ctypes.byref(loss),
+                                              _stream(stream)))
+    return w, float(loss.value)
+
+
+def mlp_predict(feats: torch.Tensor, weights: torch.Tensor, stream=None) -> torch.Tensor:
+    out = torch.empty(max(feats.shape[0], 1), dtype=torch.float32, device="cuda")
+    _check("nh_mlp_predict", lib().nh_mlp_predict(_dptr(feats.contiguous()), feats.shape[0], _dptr(weights),
+                                                  _dptr(out), _stream(stream)))
+    return out[: feats.shape[0]]
+
+
+def count_s_cliques_partitioned(o: Oriented, ri: RIndex, s: int, vertex_cost: torch.Tensor,
+                                cnt: torch.Tensor | None = None, stream=None):
+    if cnt is None:
+        cnt = torch.empty(max(ri.n_r, 1), dtype=torch.int32, device="cuda")
+    n_s = ctypes.c_uint64()
+    _check("nh_count_s_cliques_partitioned", lib().nh_count_s_cliques_partitioned(
+        o.handle, ri.handle, s, _dptr(vertex_cost.contiguous()), _dptr(cnt), ctypes.byref(n_s), _stream(stream)))
+    return cnt[: ri.n_r], int(n_s.value)
 
 
 def kernel_launches() -> int:
