@@ -166,6 +166,22 @@ int nh_mlp_predict(const float* feats, int64_t n, const uint16_t* weights, float
 int nh_count_s_cliques_partitioned(const nh_oriented* o, const nh_rindex* ri, int s, const float* vertex_cost,
                                    uint32_t* cnt, uint64_t* n_s, void* stream);
 
+/* a12 -- batches of graphs.  A batch is run as the disjoint union of its graphs (vertex ids of
+ * graph g shifted by vbase[g]), so one persistent peel launch serves all of them; s-cliques never
+ * cross graphs, so every core number and hierarchy node equals that of its own graph, and the
+ * r-cliques of graph g are the union's ids [rbase[g], rbase[g+1]).  The paper has no counterpart.
+ * graphs: host array of device CSRs; off_out int64[N+1], adj_out int32[NNZ] (device, caller-
+ * allocated, N = sum of n, NNZ = sum of nnz); vbase int64[n_graphs+1] (host, written). */
+typedef struct nh_graph_desc {
+  int64_t n, nnz;
+  const int64_t* off;
+  const int32_t* adj;
+} nh_graph_desc;
+int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t* off_out, int32_t* adj_out, int64_t* vbase,
+                   void* stream);
+/* rbase int64[n_graphs+1] (host): first r-clique id of each graph of a union built from vbase */
+int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream);
+
 /* number of CUDA kernels this library has launched in the process so far (host counter) */
 int64_t nh_kernel_launches(void);
 

@@ -318,8 +318,20 @@ struct WarpLinks {
   int* cnt;
 };
 
+// key of "the component of lo already meets the component of hi at level core(lo)" in the
+// link cache (lo has the lower or equal core); the same key link_run uses for a pair of roots
+__device__ __forceinline__ unsigned long long link_key(int32_t lo, int32_t hi) {
+  return ((unsigned long long)(uint32_t)lo << 32) | (uint32_t)hi;
+}
+
 __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int32_t m,
                                        LocalStats& ls) {
+  // drop targets whose component is R's own or already known to meet R's component (roots may be
+  // stale: a stale root only misses the cache, it never matches a wrong pair)
+  const int32_t rt = uf_find(A.lk.uf, m);
+  const int32_t rr = uf_find(A.lk.uf, Rid);
+  if (rt == rr) return;
+  if (A.lk.cache && __ldcg(A.lk.cache + (nh_mix64(link_key(rt, rr)) & A.lk.cache_mask)) == link_key(rt, rr)) return;
   const int pos = atomicAdd(W.cnt, 1);
   if (pos < kLinkBuf) W.buf[pos] = (unsigned long long)(uint32_t)m;
   else link_run(A.lk, Rid, m, ls);  // buffer full (cannot happen with the flush policy): link directly
@@ -355,11 +367,14 @@ __device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int
       __syncwarp();
     }
   }
+  const int32_t rr = uf_find(A.lk.uf, Rid);
   for (int i = lane; i < n; i += 32) {
     const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
     const int32_t prev = (i == 0) ? Rid : (int32_t)(W.buf[i - 1] & 0xffffffffull);
     if (i > 0 && prev == cur) continue;
     link_run(A.lk, prev, cur, ls);
+    // the chain implies that cur's component meets R's: remember it for later targets
+    if (A.lk.cache) A.lk.cache[nh_mix64(link_key(cur, rr)) & A.lk.cache_mask] = link_key(cur, rr);
   }
   __syncwarp();
   if (lane == 0) *W.cnt = 0;

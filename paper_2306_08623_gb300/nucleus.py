@@ -65,6 +65,8 @@ def lib():
             "nh_version": (I32, []),
             "nh_kernel_launches": (I64, []),
             "nh_vertex_features": (I32, [P, P, P]),
+            "nh_batch_union": (I32, [P, I32, P, P, P, P]),
+            "nh_rindex_bases": (I32, [P, P, I32, P, P]),
             "nh_listing_cost": (I32, [P, P, I32, P, P]),
             "nh_degree_cost": (I32, [P, I32, P, P]),
             "nh_mlp_train": (I32, [P, P, I64, I64, I32, ctypes.c_float, ctypes.c_uint64, P,
@@ -259,6 +261,36 @@ def count_s_cliques_partitioned(o: Oriented, ri: RIndex, s: int, vertex_cost: to
     _check("nh_count_s_cliques_partitioned", lib().nh_count_s_cliques_partitioned(
         o.handle, ri.handle, s, _dptr(vertex_cost.contiguous()), _dptr(cnt), ctypes.byref(n_s), _stream(stream)))
     return cnt[: ri.n_r], int(n_s.value)
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("off", ctypes.c_void_p), ("adj", ctypes.c_void_p)]
+
+
+def batch_union(graphs, stream=None):
+    """graphs: list of (off, adj) device tensors -> (off, adj, vbase list) of their disjoint union."""
+    import numpy as np
+    descs = (GraphDesc * len(graphs))()
+    N = NNZ = 0
+    for i, (off, adj) in enumerate(graphs):
+        descs[i] = GraphDesc(off.numel() - 1, adj.numel(), off.data_ptr(), adj.data_ptr() if adj.numel() else None)
+        N += off.numel() - 1
+        NNZ += adj.numel()
+    off_u = torch.empty(N + 1, dtype=torch.int64, device="cuda")
+    adj_u = torch.empty(max(NNZ, 1), dtype=torch.int32, device="cuda")
+    vbase = np.zeros(len(graphs) + 1, dtype=np.int64)
+    _check("nh_batch_union", lib().nh_batch_union(descs, len(graphs), _dptr(off_u), _dptr(adj_u),
+                                                  vbase.ctypes.data_as(P), _stream(stream)))
+    return off_u, adj_u[:NNZ], vbase
+
+
+def rindex_bases(ri: RIndex, vbase, stream=None):
+    import numpy as np
+    vbase = np.ascontiguousarray(vbase, dtype=np.int64)
+    out = np.zeros(len(vbase), dtype=np.int64)
+    _check("nh_rindex_bases", lib().nh_rindex_bases(ri.handle, vbase.ctypes.data_as(P), len(vbase) - 1,
+                                                    out.ctypes.data_as(P), _stream(stream)))
+    return out
 
 
 def kernel_launches() -> int:
