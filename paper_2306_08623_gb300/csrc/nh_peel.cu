@@ -318,20 +318,8 @@ struct WarpLinks {
   int* cnt;
 };
 
-// key of "the component of lo already meets the component of hi at level core(lo)" in the
-// link cache (lo has the lower or equal core); the same key link_run uses for a pair of roots
-__device__ __forceinline__ unsigned long long link_key(int32_t lo, int32_t hi) {
-  return ((unsigned long long)(uint32_t)lo << 32) | (uint32_t)hi;
-}
-
 __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int32_t m,
                                        LocalStats& ls) {
-  // drop targets whose component is R's own or already known to meet R's component (roots may be
-  // stale: a stale root only misses the cache, it never matches a wrong pair)
-  const int32_t rt = uf_find(A.lk.uf, m);
-  const int32_t rr = uf_find(A.lk.uf, Rid);
-  if (rt == rr) return;
-  if (A.lk.cache && __ldcg(A.lk.cache + (nh_mix64(link_key(rt, rr)) & A.lk.cache_mask)) == link_key(rt, rr)) return;
   const int pos = atomicAdd(W.cnt, 1);
   if (pos < kLinkBuf) W.buf[pos] = (unsigned long long)(uint32_t)m;
   else link_run(A.lk, Rid, m, ls);  // buffer full (cannot happen with the flush policy): link directly
@@ -367,14 +355,11 @@ __device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int
       __syncwarp();
     }
   }
-  const int32_t rr = uf_find(A.lk.uf, Rid);
   for (int i = lane; i < n; i += 32) {
     const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
     const int32_t prev = (i == 0) ? Rid : (int32_t)(W.buf[i - 1] & 0xffffffffull);
     if (i > 0 && prev == cur) continue;
     link_run(A.lk, prev, cur, ls);
-    // the chain implies that cur's component meets R's: remember it for later targets
-    if (A.lk.cache) A.lk.cache[nh_mix64(link_key(cur, rr)) & A.lk.cache_mask] = link_key(cur, rr);
   }
   __syncwarp();
   if (lane == 0) *W.cnt = 0;
@@ -510,7 +495,12 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
     if (hi[i] - lo[i] < hi[best] - lo[best]) best = i;
   const int64_t b0 = lo[best], b1 = hi[best];
   if (lane == 0 && sub == 0) ls.scan += (unsigned long long)(b1 - b0);
-  for (int64_t base = b0 + 32 * sub; base < b1; base += 32 * G) {
+  // s - r = 2: the G warps of the group form Gc chunk-groups of Ge warps; the Ge warps of one
+  // chunk-group scan the same 32 candidates and each expands the out-lists of every Ge-th of
+  // them, so that the expansion of one heavy candidate chunk is spread over Ge warps too
+  const int Ge = (S - R == 2) ? (G < 32 ? G : 32) : 1;
+  const int Gc = G / Ge, sc = sub / Ge, se = sub % Ge;
+  for (int64_t base = b0 + 32 * sc; base < b1; base += 32 * Gc) {
     const int64_t j = base + lane;
     bool ok = j < b1;
     int32_t w = 0;
@@ -547,7 +537,8 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
     } else {
       // s - r = 2: pairs (w, x), x in N+(w) adjacent to every vertex of R, expanded across the
       // warp so that lanes share the out-lists of the candidates found in this chunk
-      const uint32_t len = ok ? (uint32_t)(__ldg(g.ooff + w + 1) - __ldg(g.ooff + w)) : 0u;
+      const uint32_t len =
+          (ok && (lane % Ge) == se) ? (uint32_t)(__ldg(g.ooff + w + 1) - __ldg(g.ooff + w)) : 0u;
       uint32_t incl = len;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -743,10 +734,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
       const unsigned long long fs = vc->fsize;
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
-      // a small frontier gets several warps per r-clique (G, a power of two up to 64); the
+      // a small frontier gets several warps per r-clique (G, a power of two up to 1024); the
       // warps of a group take interleaved 32-entry chunks of the scanned list
       int G = 1;
-      while (G < 64 && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
+      while (G < 1024 && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
       const long long ngroups = nwarps / G;
       const long long grp = gwarp / G;
       const int sub = (int)(gwarp % G);

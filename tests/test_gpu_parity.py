@@ -258,3 +258,14 @@ def test_error_paths(nc):
     assert lib.nh_version() >= 100
     # still usable
     check(nc, off, adj, 2, 3)
+
+
+@pytest.mark.parametrize("scale,r,s", [(12, 2, 4), (13, 2, 3), (13, 1, 2), (11, 3, 4), (12, 1, 3)])
+def test_repeated_runs_deep_hierarchies(nc, scale, r, s):
+    """Concurrent link-efficient is nondeterministic in its intermediate states; every repeat must
+    still give the oracle's hierarchy (deep hierarchies: (2,4) on R-MAT 12 has 525 nodes over 993
+    levels)."""
+    off, adj = gg.rmat(scale, 16, 2)
+    ref = oracle.nucleus(off, adj, r, s)
+    for _ in range(4):
+        check(nc, off, adj, r, s, ref=ref)
