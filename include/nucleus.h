@@ -120,6 +120,24 @@ int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uin
 int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                       int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
+/* nh_construct_tree without any device allocation.  Some callers cannot allocate device memory
+ * while they run: a process whose device memory is already claimed by its own pooling allocator
+ * (a cudaMalloc would fail or fragment that pool), or a latency-bound caller for which the
+ * device-wide synchronisation that cudaMalloc / cudaFree may cause is not acceptable.  This entry
+ * point gives them the same tree as nh_construct_tree (same arguments, outputs and errors) while
+ * calling no cudaMalloc, cudaFree or other allocating routine.  The paper has no counterpart.
+ *  - Working memory is a fixed array in device memory, sized for n_r <= NH_TREE_NOALLOC_MAX
+ *    r-cliques (about 5.3 MB); every device that loads the library holds it until the process
+ *    exits.  Larger n_r returns NH_ERR_INVALID before any device work.
+ *  - The first call on a device looks up the array's device address (once per device, with that
+ *    device current); make that first call before any stream capture that includes this call.
+ *  - All calls share the one array: calls whose device work overlaps (on different streams, or
+ *    from different host threads) race and corrupt each other's results -- serialise them.
+ *  - The call synchronises `stream` before returning (it returns *n_nodes on the host). */
+#define NH_TREE_NOALLOC_MAX (1 << 18)
+int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
+                              int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
+
 /* a10 -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
  * x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta) (IEEE double, C = binom(s,r)); round t peels
  * every live r-clique with count <= t_i; after T = ceil(ln(max(n_r,2)) / log1p(delta/C)) + 1

@@ -197,6 +197,9 @@ int nh_partition_items(const nh_oriented* o, const float* vertex_cost, int64_t p
 // exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
 int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);
 int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+// block sums a scan of n entries needs, and the scan with caller-provided block-sum storage
+int nh_scan_u32_blocks(int64_t n);
+int nh_exclusive_scan_u32_into(const uint32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t st);
 
 // allocation helpers (stream ordered)
 template <typename T>

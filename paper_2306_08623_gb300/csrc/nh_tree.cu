@@ -1,6 +1,8 @@
 // nh_tree.cu -- a9: construct-tree-efficient (Alg. 5).  One node per union-find component; the
 // parent of node C is the node of find(L[C]); a node whose subtree holds one r-clique (one
 // member, no child node) is dropped and that r-clique hangs from the dropped node's parent.
+#include <mutex>
+
 #include "nh_internal.cuh"
 
 namespace {
@@ -84,6 +86,98 @@ extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf,
   }
   if (cudaGetLastError() != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   nh_free(own, st); nh_free(nch, st); nh_free(flag, st); nh_free(nid, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  if (!rc && n_nodes) *n_nodes = nn;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// nh_construct_tree_noalloc: the same tree construction with its working memory in a fixed
+// device array instead of stream-ordered allocations.
+//
+// Working memory for up to NH_TREE_NOALLOC_MAX r-cliques: three uint32 counters/flags per
+// r-clique, one int64 node id per r-clique (+1), and the scan's block sums.  The array lives in
+// every device that loads this library, for the life of the process (about 5.3 MB).  Host code
+// cannot use the array's name as a device address, so the address is looked up once per device
+// with cudaGetSymbolAddress (on that device) and kept.
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int64_t kNoAllocMax = NH_TREE_NOALLOC_MAX;
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kOwnOff = 0;
+constexpr size_t kNchOff = kOwnOff + align_up(sizeof(uint32_t) * kNoAllocMax);
+constexpr size_t kFlagOff = kNchOff + align_up(sizeof(uint32_t) * kNoAllocMax);
+constexpr size_t kNidOff = kFlagOff + align_up(sizeof(uint32_t) * kNoAllocMax);
+constexpr size_t kBsumOff = kNidOff + align_up(sizeof(int64_t) * (kNoAllocMax + 1));
+constexpr size_t kScratchBytes = kBsumOff + align_up(sizeof(int64_t) * (kNoAllocMax / 2048 + 2));
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_tree_scratch[kScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void* g_tree_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_tree_scratch_mu;
+
+// device address of g_tree_scratch on the current device (looked up on first use per device)
+int tree_scratch(unsigned char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NH_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return NH_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_tree_scratch_mu);
+  if (!g_tree_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_tree_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return NH_ERR_CUDA;
+    }
+    g_tree_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_tree_scratch_addr[dev]);
+  return NH_OK;
+}
+
+}  // namespace
+
+extern "C" int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
+                                         int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
+  if (n_r < 0 || n_r > kNoAllocMax) return NH_ERR_INVALID;
+  if (n_r > 0 && (!core || !uf || !L || !parent || !label)) return NH_ERR_INVALID;
+  if (n_r == 0) {
+    if (n_nodes) *n_nodes = 0;
+    return NH_OK;
+  }
+  unsigned char* base = nullptr;
+  int rc = tree_scratch(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* own = reinterpret_cast<uint32_t*>(base + kOwnOff);
+  uint32_t* nch = reinterpret_cast<uint32_t*>(base + kNchOff);
+  uint32_t* flag = reinterpret_cast<uint32_t*>(base + kFlagOff);
+  int64_t* nid = reinterpret_cast<int64_t*>(base + kNidOff);
+  int64_t* bsum = reinterpret_cast<int64_t*>(base + kBsumOff);
+  // the array keeps the previous call's contents: the counters must start at zero
+  if (cudaMemsetAsync(own, 0, sizeof(uint32_t) * n_r, st) != cudaSuccess ||
+      cudaMemsetAsync(nch, 0, sizeof(uint32_t) * n_r, st) != cudaSuccess)
+    return NH_ERR_CUDA;
+  const unsigned blocks = nh_blocks_for(n_r, 256, 152 * 32);
+  k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own);
+  k_tree_children<<<blocks, 256, 0, st>>>(n_r, uf, L, nch);
+  k_tree_flags<<<blocks, 256, 0, st>>>(n_r, uf, own, nch, flag);
+  nh_note_launch(3);
+  rc = nh_exclusive_scan_u32_into(flag, nid, n_r, bsum, st);
+  int64_t nn = 0;
+  if (!rc) {
+    k_tree_write<<<blocks, 256, 0, st>>>(n_r, uf, L, core, flag, nid, parent, label);
+    nh_note_launch();
+    if (cudaMemcpyAsync(&nn, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = NH_ERR_CUDA;
+  }
+  if (cudaGetLastError() != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (!rc && n_nodes) *n_nodes = nn;
   return rc;

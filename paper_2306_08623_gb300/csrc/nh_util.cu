@@ -118,3 +118,17 @@ int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStrea
 int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
   return scan_impl<int64_t>(in, out, n, st);
 }
+
+int nh_scan_u32_blocks(int64_t n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+// the same scan with caller-provided block-sum storage (nh_scan_u32_blocks(n) entries); no allocation
+int nh_exclusive_scan_u32_into(const uint32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t st) {
+  if (n < 0 || !out || !bsum) return NH_ERR_INVALID;
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), st) == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+  k_scan_reduce<uint32_t><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum);
+  k_scan_bsums<<<1, kScanThreads, 0, st>>>(bsum, nb, out + n);
+  k_scan_final<uint32_t><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bsum, out);
+  nh_note_launch(3);
+  return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}

@@ -59,6 +59,7 @@ def lib():
             "nh_count_s_cliques": (I32, [P, P, I32, P, ctypes.POINTER(ctypes.c_uint64), P]),
             "nh_peel_and_link": (I32, [P, P, I32, P, P, P, P, P, I32, ctypes.POINTER(PeelStats), P]),
             "nh_construct_tree": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
+            "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
@@ -185,6 +186,21 @@ def construct_tree(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent
     nn = I64()
     _check("nh_construct_tree", lib().nh_construct_tree(n_r, _dptr(core), _dptr(uf), _dptr(L), _dptr(parent),
                                                         _dptr(label), ctypes.byref(nn), _stream(stream)))
+    return parent[: n_r + nn.value], label[: nn.value], nn.value
+
+
+TREE_NOALLOC_MAX = 1 << 18
+
+
+def construct_tree_noalloc(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent: torch.Tensor,
+                           label: torch.Tensor, stream=None):
+    """nh_construct_tree without device allocation (n_r <= TREE_NOALLOC_MAX): the outputs are the
+    caller's tensors (parent: 2*n_r entries, label: n_r entries), the library's working memory is
+    a fixed device array shared by all calls, so overlapping calls must not be issued."""
+    n_r = core.numel()
+    nn = I64()
+    _check("nh_construct_tree_noalloc", lib().nh_construct_tree_noalloc(
+        n_r, _dptr(core), _dptr(uf), _dptr(L), _dptr(parent), _dptr(label), ctypes.byref(nn), _stream(stream)))
     return parent[: n_r + nn.value], label[: nn.value], nn.value
 
 
