@@ -65,6 +65,7 @@ struct LinkEnv {
   int32_t* uf;
   int32_t* L;
   const uint32_t* core;
+  int32_t* J;                       // jump pointers (may be null)
   unsigned long long* cache;        // lossy set of linked root pairs (may be null)
   unsigned long long cache_mask;
   int2* ovf[2];
@@ -246,9 +247,36 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
     // the one passed on: with concurrent unites, a value read from a component that has just
     // stopped being a root (or re-read after the test) could drop the fact "R meets Q at level
     // nR" -- the sequential order of the paper's loop does not survive concurrency otherwise.
+    //
+    // The walk down Q's chain (Alg. 5's call link(R, L[Q]) when ND[L[Q]] > ND[R]) continues in
+    // place.  Jump pointers shorten it: J[C] is a component known to meet C at level core(J[C]) <
+    // core(C) (every component on C's chain qualifies, and the relation only ever grows), so for
+    // core(J[C]) >= nR the call link(R, C) states exactly what link(R, J[C]) states, and no
+    // component between C and J[C] (all of core > core(J[C])) is where R belongs.  Each walk
+    // records the deepest component it passed above level nR as the jump pointer of its start.
+    const int32_t Q0 = Q;
+    int32_t deepest = -1;
+    uint32_t c_deepest = 0;
     for (unsigned int spin = 0;; ++spin) {
       if (spin > (1u << 20)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
       Q = uf_find(E.uf, Q);
+      if (E.J) {
+        const int32_t jq = __ldcg(E.J + Q);
+        if (jq >= 0) {
+          const uint32_t cj = __ldcg(E.core + jq);
+          if (cj > nR) {
+            deepest = jq;
+            c_deepest = cj;
+            Q = jq;
+            ++ls.link;
+            continue;
+          }
+          if (cj == nR) {
+            push(R, jq);
+            break;
+          }
+        }
+      }
       const int32_t LQ = __ldcg(E.L + Q);
       if (LQ < 0) {
         if (atomicCAS(E.L + Q, -1, R) == -1) {
@@ -259,7 +287,8 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
         }
         continue;  // L[Q] was set meanwhile: retry with its value
       }
-      if (__ldcg(E.core + LQ) < nR) {
+      const uint32_t cL = __ldcg(E.core + LQ);
+      if (cL < nR) {
         if (atomicCAS(E.L + Q, LQ, R) == LQ) {
           __threadfence();
           const int32_t pQ = uf_find(E.uf, Q);
@@ -269,8 +298,18 @@ __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& l
         }
         continue;
       }
-      push(R, LQ);
-      break;
+      if (cL == nR) {
+        push(R, LQ);
+        break;
+      }
+      deepest = LQ;  // ND[L[Q]] > ND[R]: continue the walk from L[Q]
+      c_deepest = cL;
+      Q = LQ;
+      ++ls.link;
+    }
+    if (E.J && deepest >= 0) {
+      const int32_t j0 = __ldcg(E.J + Q0);
+      if (j0 < 0 || c_deepest < __ldcg(E.core + j0)) E.J[Q0] = deepest;
     }
   }
 }
@@ -909,6 +948,8 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
     if ((rc = nh_alloc(&A.lk.cache, (int64_t)cap, st))) goto cleanup;
     A.lk.cache_mask = cap - 1;
     cudaMemsetAsync(A.lk.cache, 0xff, sizeof(unsigned long long) * cap, st);
+    if ((rc = nh_alloc(&A.lk.J, n_r, st))) goto cleanup;
+    cudaMemsetAsync(A.lk.J, 0xff, sizeof(int32_t) * n_r, st);
   }
   if (!exact) {
     // bucket upper ends t_i = floor(x_i), x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta), up to
@@ -967,7 +1008,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
 cleanup:
   nh_free(A.cnt, st); nh_free(A.alive[0], st); nh_free(A.alive[1], st); nh_free(A.front[0], st);
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
-  nh_free(A.lk.cache, st);
+  nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
   nh_free(thr_dev, st); nh_free(dmax, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
