@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
+    ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
+    ap.add_argument("--workload", choices=["rmat18", "cl4m", "batch512", "approx", "peel1"], default="rmat18",
+                    help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
+                         "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
+                         "exact core numbers on R-MAT 22 (2,3) and R-MAT 20 (3,4); peel1: one exact hierarchy of "
+                         "R-MAT <scale> EF16 seed 2 for --pair, for kernel profiles")
     return ap.parse_args()
 
 
@@ -334,6 +340,202 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# -------------------------------------------------------------------------------------------------
+# further workloads (one JSON line each; not the headline step)
+# -------------------------------------------------------------------------------------------------
+
+def _ev():
+    import torch
+    e = torch.cuda.Event(enable_timing=True)
+    e.record()
+    return e
+
+
+def _ms(a, b):
+    import torch
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_cl4m(args):
+    """Chung-Lu n = 4M, exponent 2.1, mean degree 20, plus 400 groups x 5 nested planted cliques of
+    size U[10,60] (2,000 cliques), seed 3.  Counting time for (2,3) and (3,4) with the plain
+    work distribution, the degree-cost partition and the learned-cost partition (MLP trained on
+    the costs measured on a second graph of the same recipe, seed 4, n = 1M); all three must give
+    identical counts."""
+    import numpy as np
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    tr_off, tr_adj = gg.chung_lu(1 << 20, 2.1, 20.0, 4, groups=100, per_group=5)
+    off, adj = gg.chung_lu(4 << 20, 2.1, 20.0, 3, groups=400, per_group=5)
+    d = lambda a: torch.from_numpy(a).cuda()
+    o_tr = nc.build_orientation(d(tr_off), d(tr_adj))
+    o = nc.build_orientation(d(off), d(adj))
+    res = {}
+    for r, s in [(2, 3), (3, 4)]:
+        ri_tr = nc.index_r_cliques(o_tr, r)
+        feats_tr = nc.vertex_features(o_tr)
+        cost_tr = nc.listing_cost(o_tr, ri_tr, s)
+        a = _ev()
+        w, loss = nc.mlp_train(feats_tr, cost_tr, n_train=32768, steps=300, lr=1e-2, seed=5)
+        b = _ev()
+        train_ms = _ms(a, b)
+        del ri_tr
+        ri = nc.index_r_cliques(o, r)
+        feats = nc.vertex_features(o)
+        a = _ev()
+        pred = nc.mlp_predict(feats, w)
+        b = _ev()
+        infer_ms = _ms(a, b)
+        dcost = nc.degree_cost(o, s)
+        measured = nc.listing_cost(o, ri, s)
+        # correlation of the predictions with the measured cost on the benchmark graph
+        lm, lp, ld = (torch.log1p(x).double() for x in (measured, pred, dcost))
+        corr = lambda x, y: float(((x - x.mean()) * (y - y.mean())).mean() / (x.std() * y.std() + 1e-12))
+        times = {"plain": [], "degree": [], "learned": []}
+        ref, n_s0 = nc.count_s_cliques(o, ri, s)
+        ref = ref.clone()
+        for _ in range(args.warmup + args.steps):
+            for mode in ("plain", "degree", "learned"):
+                a = _ev()
+                if mode == "plain":
+                    cnt, ns = nc.count_s_cliques(o, ri, s)
+                else:
+                    cnt, ns = nc.count_s_cliques_partitioned(o, ri, s, dcost if mode == "degree" else pred)
+                b = _ev()
+                times[mode].append(_ms(a, b))
+                assert ns == n_s0 and torch.equal(cnt, ref), "partition changed the counts"
+        med = {k: float(np.median(v[args.warmup:])) for k, v in times.items()}
+        res["%d,%d" % (r, s)] = {"n_r": ri.n_r, "n_s": n_s0, "count_ms": med, "mlp_train_ms": train_ms,
+                                 "mlp_final_mse_log": loss, "mlp_infer_ms": infer_ms,
+                                 "corr_log_cost": {"learned": corr(lm, lp), "degree": corr(lm, ld)}}
+        del ri, feats, pred, dcost, measured, ref
+    tot = {k: sum(v["count_ms"][k] for v in res.values()) for k in ("plain", "degree", "learned")}
+    line = {"metric": "s-clique counting time, learned vs degree work partition", "value": tot["learned"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "int32 counts; bf16 weights / fp32 accumulation (MLP)", "data": "synthetic",
+            "config": {"workload": "Chung-Lu n=4194304 beta 2.1 mean degree 20 + 2000 planted nested cliques "
+                                   "U[10,60], seed 3; estimator trained on the same recipe n=1048576 seed 4",
+                       "pairs": res, "total_ms": tot}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch512(args):
+    """512 graphs, seeds 1000..1511 (n log-uniform in [1e3, 2e5], mean degree U[8,40], families
+    Erdos-Renyi / R-MAT / Chung-Lu + planted cliques): exact (2,3) and (3,4) hierarchies of every
+    graph, one by one versus as one batched union (one persistent peel launch per pair)."""
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    n_graphs = 512
+    graphs = [gg.batch_member(1000 + i) for i in range(n_graphs)]
+    dev = [(torch.from_numpy(o).cuda(), torch.from_numpy(a).cuda()) for o, a in graphs]
+    tot_m = sum(len(a) // 2 for _, a in graphs)
+    res = {}
+    for r, s in [(2, 3), (3, 4)]:
+        t_one, t_batch = [], []
+        n_s = 0
+        for it in range(args.warmup + args.steps):
+            a = _ev()
+            n_s = 0
+            for off_t, adj_t in dev:
+                out = nc.hierarchy(off_t, adj_t, r, s)
+                n_s += out["n_s"]
+            b = _ev()
+            t_one.append(_ms(a, b))
+            a = _ev()
+            off_u, adj_u, vbase = nc.batch_union(dev)
+            out = nc.hierarchy(off_u, adj_u, r, s)
+            b = _ev()
+            t_batch.append(_ms(a, b))
+            assert out["n_s"] == n_s
+        res["%d,%d" % (r, s)] = {"n_s": n_s, "one_by_one_ms": sum(t_one[args.warmup:]) / args.steps,
+                                 "batched_ms": sum(t_batch[args.warmup:]) / args.steps}
+    tot_one = sum(v["one_by_one_ms"] for v in res.values())
+    tot_b = sum(v["batched_ms"] for v in res.values())
+    line = {"metric": "512-graph exact hierarchy batch time", "value": tot_b, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": "512 graphs seeds 1000-1511, %d edges in total, exact (2,3) "
+                                                        "and (3,4)" % tot_m, "pairs": res,
+                                            "one_by_one_ms": tot_one, "speedup": tot_one / tot_b}}
+    print(json.dumps(line), flush=True)
+
+
+def run_peel1(args):
+    """One exact hierarchy (orientation, index, count, peel, tree) of R-MAT <scale> EF16 seed 2 for
+    one (r,s) pair after one warm-up run: a small, fixed launch sequence for kernel profiles."""
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    r, s = (int(x) for x in args.pair.split(","))
+    off, adj = gg.rmat(args.scale, 16, 2)
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    for _ in range(2):
+        a = _ev()
+        res = nc.hierarchy(d_off, d_adj, r, s, stats=True)
+        b = _ev()
+    line = {"metric": "exact hierarchy time", "value": _ms(a, b), "unit": "ms", "higher_is_better": False,
+            "config": {"workload": "R-MAT scale %d EF16 seed 2 (%d,%d)" % (args.scale, r, s), "n_r": res["n_r"],
+                       "n_s": res["n_s"], "nodes": res["n_nodes"], "stats": res["stats"]}}
+    print(json.dumps(line), flush=True)
+
+
+def run_approx(args):
+    """Approximate core numbers (Alg. 2) beside the exact GPU run: (2,3) on R-MAT 22 EF16 seed 4,
+    (3,4) on R-MAT 20 EF16 seed 3, delta in {0.1, 0.5}: time, speedup over the exact peel, and the
+    mean / max multiplicative error over r-cliques of exact core >= 1."""
+    import numpy as np
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    out = {}
+    for scale, seed, r, s in [(22, 4, 2, 3), (20, 3, 3, 4)]:
+        off, adj = gg.rmat(scale, 16, seed)
+        o = nc.build_orientation(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda())
+        del off, adj
+        ri = nc.index_r_cliques(o, r)
+        cnt, n_s = nc.count_s_cliques(o, ri, s)
+        a = _ev()
+        pk = nc.peel_and_link(o, ri, s, cnt, stats=True)
+        b = _ev()
+        exact_ms = _ms(a, b)
+        core = pk["core"].double()
+        entry = {"n_r": ri.n_r, "n_s": n_s, "exact_peel_ms": exact_ms, "exact_rounds": pk["stats"]["rounds"]}
+        del pk
+        nz = core > 0
+        for delta in (0.1, 0.5):
+            ts = []
+            for _ in range(max(1, args.steps)):
+                a = _ev()
+                ap = nc.approx_nucleus(o, ri, s, delta, cnt, stats=True)
+                b = _ev()
+                ts.append(_ms(a, b))
+            ratio = ap["approx"].double()[nz] / core[nz]
+            C = {(2, 3): 3, (3, 4): 4}[(r, s)]
+            entry["delta_%g" % delta] = {"approx_peel_ms": float(np.median(ts)), "rounds": ap["stats"]["rounds"],
+                                         "speedup_vs_exact": exact_ms / float(np.median(ts)),
+                                         "mean_err": float(ratio.mean()), "max_err": float(ratio.max()),
+                                         "bound": (C + delta) * (1 + delta),
+                                         "within_bound": bool((ratio >= 1).all() and (ratio <= (C + delta) * (1 + delta) + 1e-9).all())}
+        out["RMAT%d (%d,%d)" % (scale, r, s)] = entry
+        del ri, cnt, core, o
+        torch.cuda.empty_cache()
+    line = {"metric": "approximate vs exact core numbers", "value": out["RMAT22 (2,3)"]["delta_0.1"]["speedup_vs_exact"],
+            "unit": "x speedup (RMAT22 (2,3), delta 0.1)", "higher_is_better": True, "n_gpus": 1, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": "R-MAT 22 EF16 seed 4 (2,3); R-MAT 20 EF16 seed 3 (3,4)",
+                                            "results": out}}
+    print(json.dumps(line), flush=True)
+
+
 def _source_hash() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -348,6 +550,14 @@ def main():
     assert args.warmup >= 0 and args.steps >= 1
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cl4m":
+        run_cl4m(args)
+    elif args.workload == "batch512":
+        run_batch512(args)
+    elif args.workload == "approx":
+        run_approx(args)
+    elif args.workload == "peel1":
+        run_peel1(args)
     else:
         run_ours(args)
 

@@ -138,6 +138,16 @@ int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int3
 int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                               int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
+/* §7.4 practical two-phase hierarchy (anh-te), from final core numbers: levels c = kmax .. 1 are
+ * processed with one union-find; at level c every r-clique of core c re-lists its s-cliques and
+ * joins the members of those whose least member core is c (the definition of §3); each component
+ * holding an r-clique of core c then gets a node at level c that adopts the top nodes of the
+ * components it absorbed.  Same output layout as nh_construct_tree (parent int32[2*n_r], label
+ * uint32[n_r], *n_nodes host); single-leaf nodes never arise.
+ * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_TIMEOUT, NH_ERR_OVERFLOW, NH_ERR_CUDA. */
+int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
+                           int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
+
 /* a10 -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
  * x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta) (IEEE double, C = binom(s,r)); round t peels
  * every live r-clique with count <= t_i; after T = ceil(ln(max(n_r,2)) / log1p(delta/C)) + 1

@@ -86,6 +86,10 @@ struct PeelArgs {
   int n_thr;
   uint32_t T;
   int link_mode;          // 0 definitional, 1 pairwise, -1 none
+  int union_mode;         // two-phase hierarchy: re-listing unites instead of peeling
+  int32_t* touched;       // two-phase: roots joined at the current level
+  unsigned long long* touched_n;
+  unsigned long long touched_cap;
   int stats;
   unsigned long long timeout_ns;
   LinkEnv lk;
@@ -355,10 +359,24 @@ constexpr int kLinkBuf = 256;
 struct WarpLinks {
   unsigned long long* buf;
   int* cnt;
+  int32_t* seen;  // kSeen roots this warp has already chained from the current R (direct-mapped)
 };
+
+constexpr int kSeen = 64;
+
+// warp-collective: forget the roots seen for the previous frontier r-clique
+__device__ __forceinline__ void wl_begin(const WarpLinks& W, int lane) {
+  __syncwarp();
+  for (int i = lane; i < kSeen; i += 32) W.seen[i] = -1;
+  __syncwarp();
+}
 
 __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int32_t m,
                                        LocalStats& ls) {
+  // a target whose component this warp has already chained from R adds nothing: R meets that
+  // whole component at its level already (a root that changed since only misses the filter)
+  const int32_t rt = uf_find(A.lk.uf, m);
+  if (W.seen[rt & (kSeen - 1)] == rt) return;
   const int pos = atomicAdd(W.cnt, 1);
   if (pos < kLinkBuf) W.buf[pos] = (unsigned long long)(uint32_t)m;
   else link_run(A.lk, Rid, m, ls);  // buffer full (cannot happen with the flush policy): link directly
@@ -401,6 +419,11 @@ __device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int
     link_run(A.lk, prev, cur, ls);
   }
   __syncwarp();
+  for (int i = lane; i < n; i += 32) {  // record after every link of the chain has completed
+    const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
+    W.seen[cur & (kSeen - 1)] = cur;
+  }
+  __syncwarp();
   if (lane == 0) *W.cnt = 0;
   __syncwarp();
 }
@@ -415,6 +438,34 @@ __device__ __forceinline__ void wl_maybe_flush(const WarpLinks& W, const PeelArg
 template <int CM, bool EXACT>
 __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM], uint32_t t,
                                           uint32_t thr, int32_t* nf, const WarpLinks& W, LocalStats& ls) {
+  if (A.union_mode) {
+    // two-phase hierarchy at level thr (= core of Rid): an s-clique whose least member core is
+    // thr joins all its members; its member of least id among those of core thr does it
+    int32_t attr = Rid;
+#pragma unroll
+    for (int j = 0; j < CM; j++) {
+      const uint32_t c = __ldcg(A.val + mem[j]);
+      if (c < thr) return;
+      if (c == thr && mem[j] < attr) attr = mem[j];
+    }
+    ls.listed++;
+    if (attr != Rid) return;
+#pragma unroll
+    for (int j = 0; j < CM; j++) {
+      const int32_t child = uf_unite(A.lk.uf, Rid, mem[j], A.lk.ctl);
+      if (child >= 0) {
+        ls.unite++;
+        const unsigned long long pos = atomicAdd(A.touched_n, 2ull);
+        if (pos + 1 < A.touched_cap) {
+          A.touched[pos] = child;
+          A.touched[pos + 1] = uf_find(A.lk.uf, child);
+        } else {
+          atomicCAS(&A.lk.ctl->err, 0, NH_ERR_OVERFLOW);
+        }
+      }
+    }
+    return;
+  }
   uint32_t rd[CM];
   bool dead = false;
   int32_t attr = Rid;
@@ -462,6 +513,7 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 template <int R, int S, bool EXACT>
 __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
                             int sub, int G, const WarpLinks& W, LocalStats& ls) {
+  if constexpr (EXACT) wl_begin(W, lane);
   constexpr int kPerLane = (S - R == 1) ? R : 5;  // link targets one lane can add per converged step
   const GView& g = A.g;
   int32_t vx[3] = {0, 0, 0};
@@ -706,9 +758,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
   __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
   __shared__ int s_lcnt[kThreads / 32];
+  __shared__ int32_t s_seen[kThreads / 32][kSeen];
   if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
-  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5]};
+  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
   for (;;) {
     if (vc->done || vc->err) break;
     if (vc->need_scan) {
@@ -1059,6 +1112,227 @@ extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int
     nh_note_launch();
   }
   nh_free(E.ctl, st); nh_free(E.ovf[0], st); nh_free(E.ovf[1], st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// §7.4 practical two-phase hierarchy (anh-te): with the core numbers known, levels are processed
+// from the largest core down to 1 with one union-find: at level c every r-clique of core c
+// re-lists its s-cliques and joins the members of those whose least core is c; then every
+// component holding an r-clique of core c gets a node at level c, which adopts the previous top
+// nodes of the components it absorbed.  One persistent cooperative kernel, four grid barriers
+// per level.
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+struct TreeOut {
+  const int32_t* order;    // r-cliques sorted by core (any order within a level)
+  const int64_t* lvl_off;  // [kmax + 2]
+  uint32_t kmax;
+  uint32_t* lvl;           // per root: last level it got a node
+  int32_t* nid;            // per root: that node
+  int32_t* top;            // per root: current top node of its component
+  int32_t* parent;         // [n_r + nodes]
+  uint32_t* label;
+  unsigned long long* node_count;
+};
+
+template <int R, int S>
+__global__ void __launch_bounds__(kThreads) k_two_phase(PeelArgs A, TreeOut T) {
+  PeelCtl* ctl = A.lk.ctl;
+  volatile PeelCtl* vc = ctl;
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
+  __shared__ int s_lcnt[kThreads / 32];
+  __shared__ int32_t s_seen[kThreads / 32][kSeen];
+  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
+  __syncwarp();
+  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
+  const int64_t n_r = A.n_r;
+  for (uint32_t level = T.kmax; level >= 1; --level) {
+    const int64_t lo = T.lvl_off[level], hi = T.lvl_off[level + 1];
+    const unsigned long long cnt = (unsigned long long)(hi - lo);
+    if (cnt == 0) continue;
+    // unions at this level
+    {
+      int G = 1;
+      while (G < 1024 && (unsigned long long)(2 * G) * cnt <= (unsigned long long)nwarps) G *= 2;
+      const long long ngroups = nwarps / G, grp = gwarp / G;
+      const int sub = (int)(gwarp % G);
+      if (grp < ngroups)
+        for (unsigned long long it = (unsigned long long)grp; it < cnt; it += (unsigned long long)ngroups)
+          relist_item<R, S, true>(A, T.order[lo + it], 0u, level, nullptr, lane, sub, G, W, ls);
+    }
+    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
+    // a node for every component holding an r-clique of this level
+    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
+      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
+      uint32_t cur = __ldcg(T.lvl + y);
+      while (cur != level) {
+        const uint32_t prev = atomicCAS(T.lvl + y, cur, level);
+        if (prev == cur) {
+          const int32_t id = (int32_t)atomicAdd(T.node_count, 1ull);
+          T.nid[y] = id;
+          T.label[id] = level;
+          T.parent[n_r + id] = -1;
+          break;
+        }
+        cur = prev;
+      }
+    }
+    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
+    // leaves of this level, and previous top nodes of every joined component
+    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
+      const int32_t R0 = T.order[lo + i];
+      T.parent[R0] = __ldcg(T.nid + uf_find(A.lk.uf, R0));
+    }
+    {
+      const unsigned long long nt = *(volatile unsigned long long*)A.touched_n;
+      for (unsigned long long i = (unsigned long long)gtid; i < nt; i += (unsigned long long)nthreads) {
+        const int32_t x = __ldcg(A.touched + i);
+        const int32_t tp = __ldcg(T.top + x);
+        if (tp >= 0) T.parent[n_r + tp] = __ldcg(T.nid + uf_find(A.lk.uf, x));
+      }
+    }
+    if (!grid_sync(ctl, A.timeout_ns, [&] { *A.touched_n = 0; })) break;
+    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
+      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
+      T.top[y] = __ldcg(T.nid + y);
+    }
+    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
+  }
+  if (A.stats) {
+    const unsigned long long v0 = warp_sum_u64(ls.listed), v3 = warp_sum_u64(ls.unite);
+    if (lane == 0) {
+      atomicAdd(&ctl->st_listed, v0);
+      atomicAdd(&ctl->st_unite, v3);
+    }
+  }
+}
+
+__global__ void k_core_hist(int64_t n_r, const uint32_t* __restrict__ core, uint32_t* __restrict__ hist) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(hist + core[i], 1u);
+}
+
+__global__ void k_core_scatter(int64_t n_r, const uint32_t* __restrict__ core, const int64_t* __restrict__ off,
+                               unsigned long long* __restrict__ cursor, int32_t* __restrict__ order) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = core[i];
+    order[off[c] + (int64_t)atomicAdd(cursor + c, 1ull)] = (int32_t)i;
+  }
+}
+
+__global__ void k_two_phase_init(int64_t n_r, int32_t* __restrict__ uf, uint32_t* __restrict__ lvl,
+                                 int32_t* __restrict__ top, int32_t* __restrict__ parent) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
+    uf[i] = (int32_t)i;
+    lvl[i] = 0;
+    top[i] = -1;
+    parent[i] = -1;
+  }
+}
+
+template <int R, int S>
+int launch_two_phase(PeelArgs& A, TreeOut& T, cudaStream_t st) {
+  const void* fn = (const void*)k_two_phase<R, S>;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1) return NH_ERR_CUDA;
+  void* args[] = {&A, &T};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(sms * per)), dim3(kThreads), args, 0, st);
+  nh_note_launch();
+  return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
+                                      int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
+  if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
+  const int r = ri->r;
+  if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
+  const int64_t n_r = ri->n_r;
+  if (n_r == 0) {
+    if (n_nodes) *n_nodes = 0;
+    return NH_OK;
+  }
+  if (!core || !parent || !label) return NH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  PeelArgs A{};
+  TreeOut T{};
+  A.g = make_view(o, ri);
+  A.n_r = n_r;
+  A.val = const_cast<uint32_t*>(core);
+  A.union_mode = 1;
+  A.link_mode = -1;
+  A.stats = 0;
+  A.timeout_ns = 60ull * 1000000000ull;
+  A.touched_cap = 2ull * (unsigned long long)n_r + 64;
+  unsigned int* dmax = nullptr;
+  uint32_t* hist = nullptr;
+  int64_t* off = nullptr;
+  unsigned long long* cursor = nullptr;
+  int32_t* order = nullptr;
+  int rc = NH_OK;
+  unsigned int kmax = 0;
+  if ((rc = nh_alloc(&A.lk.uf, n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) || (rc = nh_alloc(&A.touched, (int64_t)A.touched_cap, st)) ||
+      (rc = nh_alloc(&A.touched_n, 1, st)) || (rc = nh_alloc(&T.lvl, n_r, st)) || (rc = nh_alloc(&T.nid, n_r, st)) ||
+      (rc = nh_alloc(&T.top, n_r, st)) || (rc = nh_alloc(&T.node_count, 1, st)) || (rc = nh_alloc(&dmax, 1, st)) ||
+      (rc = nh_alloc(&order, n_r, st)))
+    goto cleanup;
+  cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
+  k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, core, dmax);
+  nh_note_launch();
+  cudaMemcpyAsync(&kmax, dmax, sizeof(kmax), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
+  if ((rc = nh_alloc(&hist, (int64_t)kmax + 2, st)) || (rc = nh_alloc(&off, (int64_t)kmax + 3, st)) ||
+      (rc = nh_alloc(&cursor, (int64_t)kmax + 2, st)))
+    goto cleanup;
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kmax + 2), st);
+  cudaMemsetAsync(cursor, 0, sizeof(unsigned long long) * (kmax + 2), st);
+  k_core_hist<<<nh_blocks_for(n_r, 256, 152 * 16), 256, 0, st>>>(n_r, core, hist);
+  nh_note_launch();
+  if ((rc = nh_exclusive_scan_u32(hist, off, (int64_t)kmax + 2, st))) goto cleanup;
+  k_core_scatter<<<nh_blocks_for(n_r, 256, 152 * 16), 256, 0, st>>>(n_r, core, off, cursor, order);
+  k_two_phase_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, A.lk.uf, T.lvl, T.top, parent);
+  nh_note_launch(2);
+  cudaMemsetAsync(A.lk.ctl, 0, sizeof(PeelCtl), st);
+  cudaMemsetAsync(A.touched_n, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(T.node_count, 0, sizeof(unsigned long long), st);
+  T.order = order;
+  T.lvl_off = off;
+  T.kmax = kmax;
+  T.parent = parent;
+  T.label = label;
+  if (kmax >= 1) {
+    if (r == 1 && s == 2) rc = launch_two_phase<1, 2>(A, T, st);
+    else if (r == 1 && s == 3) rc = launch_two_phase<1, 3>(A, T, st);
+    else if (r == 2 && s == 3) rc = launch_two_phase<2, 3>(A, T, st);
+    else if (r == 2 && s == 4) rc = launch_two_phase<2, 4>(A, T, st);
+    else rc = launch_two_phase<3, 4>(A, T, st);
+  }
+  if (!rc) {
+    PeelCtl h{};
+    unsigned long long nn = 0;
+    cudaMemcpyAsync(&h, A.lk.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&nn, T.node_count, sizeof(nn), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
+    else if (h.err) rc = h.err;
+    if (!rc && n_nodes) *n_nodes = (int64_t)nn;
+  }
+cleanup:
+  nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
+  nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
+  nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }

@@ -60,6 +60,7 @@ def lib():
             "nh_peel_and_link": (I32, [P, P, I32, P, P, P, P, P, I32, ctypes.POINTER(PeelStats), P]),
             "nh_construct_tree": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
+            "nh_hierarchy_two_phase": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
@@ -186,6 +187,18 @@ def construct_tree(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent
     nn = I64()
     _check("nh_construct_tree", lib().nh_construct_tree(n_r, _dptr(core), _dptr(uf), _dptr(L), _dptr(parent),
                                                         _dptr(label), ctypes.byref(nn), _stream(stream)))
+    return parent[: n_r + nn.value], label[: nn.value], nn.value
+
+
+def hierarchy_two_phase(o: Oriented, ri: RIndex, s: int, core: torch.Tensor, stream=None):
+    """§7.4 two-phase hierarchy from final core numbers; returns (parent, label, n_nodes) like
+    construct_tree."""
+    n_r = ri.n_r
+    parent = torch.empty(max(2 * n_r, 1), dtype=torch.int32, device="cuda")
+    label = torch.empty(max(n_r, 1), dtype=torch.int32, device="cuda")
+    nn = I64()
+    _check("nh_hierarchy_two_phase", lib().nh_hierarchy_two_phase(o.handle, ri.handle, s, _dptr(core), _dptr(parent),
+                                                                  _dptr(label), ctypes.byref(nn), _stream(stream)))
     return parent[: n_r + nn.value], label[: nn.value], nn.value
 
 

@@ -269,3 +269,23 @@ def test_repeated_runs_deep_hierarchies(nc, scale, r, s):
     ref = oracle.nucleus(off, adj, r, s)
     for _ in range(4):
         check(nc, off, adj, r, s, ref=ref)
+
+
+@pytest.mark.parametrize("r,s", SUPPORTED)
+def test_two_phase_hierarchy(nc, r, s):
+    """§7.4 two-phase hierarchy from the GPU core numbers equals the oracle's hierarchy."""
+    graphs = [gg.rmat(11, 8, 3), gg.erdos_renyi(2000, 16000, 1), gg.complete(7), gg.from_edges(5, []),
+              gg.chung_lu(3000, 2.1, 10, 5, groups=6, per_group=5, size_lo=6, size_hi=14)]
+    rng = np.random.default_rng(99 + r + s)
+    for _ in range(8):
+        graphs.append(gg.gnp(int(rng.integers(4, 14)), float(rng.uniform(0.4, 0.95)), int(rng.integers(1 << 30))))
+    for off, adj in graphs:
+        d_off, d_adj = to_dev(off, adj)
+        o = nc.build_orientation(d_off, d_adj)
+        ri = nc.index_r_cliques(o, r)
+        cnt, _ = nc.count_s_cliques(o, ri, s)
+        pk = nc.peel_and_link(o, ri, s, cnt)
+        parent, label, nn = nc.hierarchy_two_phase(o, ri, s, pk["core"])
+        ref = oracle.nucleus(off, adj, r, s)
+        compare_hierarchy(parent.cpu().numpy(), u32(label), nn, ref["leaf_node"], ref["node_parent"],
+                          ref["node_label"])
