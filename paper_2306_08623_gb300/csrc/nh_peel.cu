@@ -387,7 +387,9 @@ __device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int
   __syncwarp();
   const int n = min(*(volatile int*)W.cnt, kLinkBuf);
   if (n == 0) return;
-  for (int i = lane; i < kLinkBuf; i += 32) {
+  int P = 2;  // sort only the smallest power of two holding the n entries
+  while (P < n) P <<= 1;
+  for (int i = lane; i < P; i += 32) {
     unsigned long long key = ~0ull;
     if (i < n) {
       const int32_t rt = uf_find(A.lk.uf, (int32_t)W.buf[i]);
@@ -397,9 +399,9 @@ __device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int
     W.buf[i] = key;
   }
   __syncwarp();
-  for (int k = 2; k <= kLinkBuf; k <<= 1) {
+  for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < kLinkBuf; i += 32) {
+      for (int i = lane; i < P; i += 32) {
         const int ixj = i ^ j;
         if (ixj > i) {
           const unsigned long long a = W.buf[i], b = W.buf[ixj];
