@@ -210,6 +210,12 @@ int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t* off_out, 
 /* rbase int64[n_graphs+1] (host): first r-clique id of each graph of a union built from vbase */
 int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream);
 
+/* Tuning knob of the peel and two-phase kernels (process-wide, default 1024): the largest number
+ * of warps that share one frontier r-clique when the frontier is small.  More warps shorten a
+ * round's critical path; with link-efficient each warp chains its own link targets, so more
+ * warps also repeat walks.  g: power of two in [1, 1024].  Results never depend on it. */
+int nh_set_peel_max_group(int g);
+
 /* number of CUDA kernels this library has launched in the process so far (host counter) */
 int64_t nh_kernel_launches(void);
 

@@ -25,6 +25,8 @@
 
 #include "nh_internal.cuh"
 
+static int g_peel_max_group = 1024;  // set by nh_set_peel_max_group
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -87,6 +89,7 @@ struct PeelArgs {
   uint32_t T;
   int link_mode;          // 0 definitional, 1 pairwise, -1 none
   int union_mode;         // two-phase hierarchy: re-listing unites instead of peeling
+  int gmax;               // largest number of warps per frontier r-clique (power of two)
   int32_t* touched;       // two-phase: roots joined at the current level
   unsigned long long* touched_n;
   unsigned long long touched_cap;
@@ -831,7 +834,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
       // a small frontier gets several warps per r-clique (G, a power of two up to 1024); the
       // warps of a group take interleaved 32-entry chunks of the scanned list
       int G = 1;
-      while (G < 1024 && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
+      while (G < A.gmax && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
       const long long ngroups = nwarps / G;
       const long long grp = gwarp / G;
       const int sub = (int)(gwarp % G);
@@ -981,6 +984,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   A.round = round;
   A.link_mode = exact ? link_mode : -1;
   A.stats = stats != nullptr;
+  A.gmax = g_peel_max_group;
   A.timeout_ns = 60ull * 1000000000ull;
   A.lk.uf = uf;
   A.lk.L = L;
@@ -1165,7 +1169,7 @@ __global__ void __launch_bounds__(kThreads) k_two_phase(PeelArgs A, TreeOut T) {
     // unions at this level
     {
       int G = 1;
-      while (G < 1024 && (unsigned long long)(2 * G) * cnt <= (unsigned long long)nwarps) G *= 2;
+      while (G < A.gmax && (unsigned long long)(2 * G) * cnt <= (unsigned long long)nwarps) G *= 2;
       const long long ngroups = nwarps / G, grp = gwarp / G;
       const int sub = (int)(gwarp % G);
       if (grp < ngroups)
@@ -1275,6 +1279,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   A.n_r = n_r;
   A.val = const_cast<uint32_t*>(core);
   A.union_mode = 1;
+  A.gmax = g_peel_max_group;
   A.link_mode = -1;
   A.stats = 0;
   A.timeout_ns = 60ull * 1000000000ull;
@@ -1337,4 +1342,10 @@ cleanup:
   nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
+}
+
+extern "C" int nh_set_peel_max_group(int g) {
+  if (g < 1 || g > 1024 || (g & (g - 1))) return NH_ERR_INVALID;
+  g_peel_max_group = g;
+  return NH_OK;
 }

@@ -61,6 +61,7 @@ def lib():
             "nh_construct_tree": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_hierarchy_two_phase": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
+            "nh_set_peel_max_group": (I32, [I32]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
@@ -320,6 +321,33 @@ def rindex_bases(ri: RIndex, vbase, stream=None):
     _check("nh_rindex_bases", lib().nh_rindex_bases(ri.handle, vbase.ctypes.data_as(P), len(vbase) - 1,
                                                     out.ctypes.data_as(P), _stream(stream)))
     return out
+
+
+def set_peel_max_group(g: int):
+    """Largest number of warps per frontier r-clique (power of two, 1..1024); results never
+    depend on it."""
+    _check("nh_set_peel_max_group", lib().nh_set_peel_max_group(int(g)))
+
+
+def autotune_peel_max_group(run, candidates=(16, 64, 256, 1024), repeats: int = 1) -> dict:
+    """Time `run()` (a callable doing one timed piece of work on the device) under each
+    candidate warps-per-r-clique cap; keep the fastest cap set and return all timings (ms)."""
+    times = {}
+    for g in candidates:
+        set_peel_max_group(g)
+        best = None
+        for _ in range(repeats):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            run()
+            b.record()
+            b.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        times[g] = best
+    set_peel_max_group(min(times, key=times.get))
+    return times
 
 
 def kernel_launches() -> int:
