@@ -177,6 +177,22 @@ def algorithmic_peel_bytes(stats: dict, r: int, s: int) -> int:
             + 16 * stats["hash_probes"] + 8 * stats["link_calls"] + 12 * stats["frontier_total"])
 
 
+def reduce_max(value: float, device=None) -> float:
+    """Max of a per-rank number over all ranks (the replicas' time; one rank: unchanged)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Units all ranks processed per second of the slowest rank (independent replicas)."""
+    return world * units_per_rank * steps / (max_ms / 1000.0)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -248,15 +264,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = nc.kernel_launches() - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
+    total_ms = reduce_max(sum(step_ms), dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
-    value = world * n_s_tot * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(n_s_tot, world, args.steps, total_ms)
+
+    # beside the timed step: the §7.4 two-phase hierarchy (anh-te) from the same core numbers, once
+    two_phase_ms = {}
+    o2 = nc.build_orientation(d_off, d_adj)
+    for r, s in PAIRS:
+        ri2 = nc.index_r_cliques(o2, r)
+        cnt2, _ = nc.count_s_cliques(o2, ri2, s)
+        pk2 = nc.peel_and_link(o2, ri2, s, cnt2)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, nn2 = nc.hierarchy_two_phase(o2, ri2, s, pk2["core"])
+        b.record(stream)
+        b.synchronize()
+        two_phase_ms[(r, s)] = a.elapsed_time(b)
+        assert nn2 == info[(r, s)]["n_nodes"]
+        del ri2, cnt2, pk2
+    del o2
 
     # dominant kernel: the peel launch with the largest time
     peel_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in timers.items()}
@@ -296,13 +327,8 @@ def run_ours(args):
                 d2h += t.numel() * t.element_size()
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * n_s_tot * args.steps / (e2e_total / 1000.0)
+    e2e_total = reduce_max(sum(e2e_ms), dev)
+    e2e_value = whole_job_rate(n_s_tot, world, args.steps, e2e_total)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -315,7 +341,8 @@ def run_ours(args):
 
     if rank == 0:
         per_pair = {"%d,%d" % k: {"n_r": v["n_r"], "n_s": v["n_s"], "nodes": v["n_nodes"],
-                                  "rounds": v["stats"]["rounds"], "peel_ms": round(peel_ms[k], 3)}
+                                  "rounds": v["stats"]["rounds"], "peel_ms": round(peel_ms[k], 3),
+                                  "two_phase_hierarchy_ms": round(two_phase_ms[k], 3)}
                     for k, v in info.items()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

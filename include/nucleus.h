@@ -166,9 +166,9 @@ int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L,
                   const int32_t* pairs, int64_t n_pairs, void* stream);
 
 /* a11 -- learned work estimator for the s-clique listing (rec-list-cliques) work.
- * Work items are the out-edges (v -> a) of the orientation in CSR order; a partition gives each
- * warp of the counting kernel one contiguous item range of equal estimated cost.  Counts do not
- * depend on the partition.  The estimator is an MLP NH_MLP_FEATURES -> 64 -> 64 -> 1 (ReLU),
+ * Work items are the out-edges (v -> a) of the orientation; a cost estimate per vertex orders the
+ * items by decreasing cost, and the warps of the counting kernel take them in chunks from a shared
+ * counter (largest first).  Counts do not depend on the schedule.  The estimator is an MLP NH_MLP_FEATURES -> 64 -> 64 -> 1 (ReLU),
  * BF16 weights, FP32 accumulation, trained (Adam, full batch, MSE on log1p(cost)) on the
  * per-vertex costs that the counting kernel itself measures.  The paper has no counterpart: it
  * schedules this work with a work-stealing scheduler (§3).
@@ -190,7 +190,7 @@ int nh_mlp_train(const float* feats, const float* cost, int64_t n, int64_t n_tra
                  uint64_t seed, uint16_t* weights, float* final_loss, void* stream);
 /* pred float[n] = predicted listing cost per vertex */
 int nh_mlp_predict(const float* feats, int64_t n, const uint16_t* weights, float* pred, void* stream);
-/* nh_count_s_cliques with the items split by vertex_cost (float[n], any estimate) */
+/* nh_count_s_cliques with the items scheduled largest-first by vertex_cost (float[n], any estimate) */
 int nh_count_s_cliques_partitioned(const nh_oriented* o, const nh_rindex* ri, int s, const float* vertex_cost,
                                    uint32_t* cnt, uint64_t* n_s, void* stream);
 

@@ -28,22 +28,50 @@ __global__ void k_count_12(int64_t n, const int64_t* __restrict__ off, uint32_t*
 }
 
 // s = 3: triangles (v, a, b) with a, b in N+(v), b in N+(a)
-// Work items are out-edges (v -> a).  With bounds == null the warps stride over all items;
-// otherwise warp w takes the contiguous item range [bounds[w], bounds[w+1]).  When cost != null
+// Work items are out-edges (v -> a).  With order == null the warps stride over all items;
+// otherwise the warps take chunks of kChunk items of `order` (items sorted by decreasing
+// estimated cost) from the shared counter *next: the heaviest items start first and every warp
+// keeps taking work until none is left (largest-first dynamic scheduling).  When cost != null
 // the work of each item (list entries touched, binary-search steps included) is added to
 // cost[v]: the measured listing cost the work estimator learns.
 __device__ __forceinline__ float log2p1(int64_t x) { return log2f((float)x + 1.0f); }
 
+constexpr unsigned long long kChunk = 8;
+
+// next work item of this warp, or -1 when there is none left (warp-uniform)
+struct ItemCursor {
+  const int32_t* order;
+  unsigned long long* next;
+  int64_t m, nwarps, p;        // plain stride
+  unsigned long long cur, end; // dynamic chunk
+  __device__ __forceinline__ int64_t get(int lane) {
+    if (!order) {
+      const int64_t q = p;
+      p += nwarps;
+      return q < m ? q : -1;
+    }
+    if (cur >= end) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(next, kChunk);
+      b = __shfl_sync(NH_FULL, b, 0);
+      if (b >= (unsigned long long)m) return -1;
+      cur = b;
+      end = min(b + kChunk, (unsigned long long)m);
+    }
+    return order[cur++];
+  }
+};
+
 template <int R>
 __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
-                           const int64_t* __restrict__ bounds, float* __restrict__ cost) {
+                           const int32_t* __restrict__ order, unsigned long long* __restrict__ next,
+                           float* __restrict__ cost) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long found = 0;
-  const int64_t p0 = bounds ? bounds[warp] : warp, p1 = bounds ? bounds[warp + 1] : g.m;
-  const int64_t pst = bounds ? 1 : nwarps;
-  for (int64_t p = p0; p < p1; p += pst) {
+  ItemCursor it{order, next, g.m, nwarps, warp, 0, 0};
+  for (int64_t p = it.get(lane); p >= 0; p = it.get(lane)) {
     const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
     int64_t sb = g.ooff[v], se = g.ooff[v + 1];  // scanned list
     int64_t lb = g.ooff[a], le = g.ooff[a + 1];  // searched list
@@ -78,7 +106,8 @@ __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long lo
 template <int R>
 __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
                            int32_t* __restrict__ gscratch, int cap, int use_smem, int* __restrict__ status,
-                           const int64_t* __restrict__ bounds, float* __restrict__ cost) {
+                           const int32_t* __restrict__ order, unsigned long long* __restrict__ next,
+                           float* __restrict__ cost) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -89,9 +118,8 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
   int32_t* c2e1 = base + cap;  // edge (v, b)
   int32_t* c2e2 = base + 2 * cap;  // edge (a, b)
   unsigned long long found = 0;
-  const int64_t p0 = bounds ? bounds[warp] : warp, p1 = bounds ? bounds[warp + 1] : g.m;
-  const int64_t pst = bounds ? 1 : nwarps;
-  for (int64_t p = p0; p < p1; p += pst) {
+  ItemCursor it{order, next, g.m, nwarps, warp, 0, 0};
+  for (int64_t p = it.get(lane); p >= 0; p = it.get(lane)) {
     const int32_t v = g.osrc[p], a = g.oadj[p], e_va = g.oeid[p];
     int64_t sb = g.ooff[v], se = g.ooff[v + 1];
     int64_t lb = g.ooff[a], le = g.ooff[a + 1];
@@ -196,7 +224,8 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
   unsigned long long* dcount = nullptr;
   int* status = nullptr;
   int32_t* scratch = nullptr;
-  int64_t* bounds = nullptr;
+  int32_t* order = nullptr;
+  unsigned long long* next = nullptr;
   int rc = NH_OK;
   if ((rc = nh_alloc(&dcount, 1, st)) || (rc = nh_alloc(&status, 1, st))) {
     nh_free(dcount, st); nh_free(status, st);
@@ -209,12 +238,12 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
   if (s == 3) {
     const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
     int grid = grid_for(fn, kThreads, 0);
-    if (vertex_cost && (rc = nh_partition_items(o, vertex_cost, (int64_t)grid * kWarpsPerBlock, &bounds, st))) {
+    if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) {
       nh_free(dcount, st); nh_free(status, st);
       return rc;
     }
-    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, bounds, measure);
-    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, bounds, measure);
+    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
+    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
     nh_note_launch();
   } else {
     const int cap = (int)(o->max_out > 0 ? o->max_out : 1);
@@ -228,13 +257,13 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
       return rc;
     }
     const size_t dyn = use_smem ? smem : 0;
-    if (vertex_cost && (rc = nh_partition_items(o, vertex_cost, (int64_t)grid * kWarpsPerBlock, &bounds, st))) {
+    if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) {
       nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st);
       return rc;
     }
-    if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
-    else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
-    else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, bounds, measure);
+    if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
+    else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
+    else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
     nh_note_launch();
   }
   if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
@@ -242,7 +271,7 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
   int hs = 0;
   cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st); nh_free(bounds, st);
+  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st); nh_free(order, st); nh_free(next, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (!rc && hs) rc = hs;
   if (!rc && n_s) *n_s = hcount;

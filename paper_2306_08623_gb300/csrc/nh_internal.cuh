@@ -190,9 +190,10 @@ void nh_note_launch(int64_t k = 1);
 // (optional) selects the cost-balanced partition, measure (optional) receives per-vertex cost
 int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
                   const float* vertex_cost, float* measure, cudaStream_t st);
-// contiguous out-edge item ranges of equal total cost (nh_mlp.cu); *bounds has parts + 1 entries
-int nh_partition_items(const nh_oriented* o, const float* vertex_cost, int64_t parts, int64_t** bounds,
-                       cudaStream_t st);
+// out-edge items in decreasing estimated cost (log2 buckets) and a zeroed shared work counter for
+// dynamic scheduling (nh_mlp.cu); the caller frees both
+int nh_schedule_items(const nh_oriented* o, const float* vertex_cost, int32_t** order, unsigned long long** next,
+                      cudaStream_t st);
 
 // exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
 int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);

@@ -1,9 +1,9 @@
-// nh_mlp.cu -- a11: the learned work estimator and the cost-balanced partition of the s-clique
+// nh_mlp.cu -- a11: the learned work estimator and the cost-driven schedule of the s-clique
 // listing work.  A small MLP (8 features -> 64 -> 64 -> 1, ReLU; BF16 weights, FP32
 // accumulation) is trained on per-vertex listing costs that the counting kernel measures, and
-// predicts cost per vertex; the out-edge work items (CSR order) are then split into one
-// contiguous range per warp with equal predicted cost.  Counting results do not depend on the
-// partition; the degree cost d+(v)^(s-1) is the baseline partition.
+// predicts cost per vertex; the out-edge work items are then ordered by decreasing predicted cost
+// (log2 buckets) and handed out to warps in chunks from a shared counter, largest first.
+// Counting results do not depend on the schedule; the degree cost d+(v)^(s-1) is the baseline.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -73,29 +73,26 @@ __global__ void k_degree_cost(GView g, int s, float* __restrict__ cost) {
   }
 }
 
-// per out-edge item: its source vertex's cost spread evenly over the vertex's out-edges, in
-// integer units (at least 1)
-__global__ void k_item_units(GView g, const float* __restrict__ vcost, uint32_t* __restrict__ units) {
+// per out-edge item: its source vertex's cost spread evenly over the vertex's out-edges; the item's
+// bucket is 31 - floor(log2(cost + 1)), so bucket 0 holds the heaviest items
+__global__ void k_item_bucket(GView g, const float* __restrict__ vcost, uint8_t* __restrict__ bucket,
+                              uint32_t* __restrict__ hist) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.m; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = g.osrc[p];
     const float d = (float)(g.ooff[v + 1] - g.ooff[v]);
     const float c = fmaxf(vcost[v], 0.0f) / fmaxf(d, 1.0f);
-    units[p] = (uint32_t)fminf(fmaxf(ceilf(c), 1.0f), 1.0e6f);
+    const int lg = (int)fminf(floorf(log2f(c + 1.0f)), 31.0f);
+    const uint8_t bk = (uint8_t)(31 - lg);
+    bucket[p] = bk;
+    atomicAdd(hist + bk, 1u);
   }
 }
 
-// bounds[w] = first item whose prefix cost reaches w/parts of the total
-__global__ void k_bounds(const int64_t* __restrict__ prefix, int64_t m, int64_t parts, int64_t* __restrict__ bounds) {
-  const int64_t total = prefix[m];
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w <= parts; w += (int64_t)gridDim.x * blockDim.x) {
-    if (w == parts) { bounds[w] = m; continue; }
-    const int64_t target = (int64_t)((double)total * (double)w / (double)parts);
-    int64_t lo = 0, hi = m;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (prefix[mid] < target) lo = mid + 1; else hi = mid;
-    }
-    bounds[w] = lo;
+__global__ void k_item_scatter(int64_t m, const uint8_t* __restrict__ bucket, const int64_t* __restrict__ off,
+                               unsigned long long* __restrict__ cursor, int32_t* __restrict__ order) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t bk = bucket[p];
+    order[off[bk] + (int64_t)atomicAdd(cursor + bk, 1ull)] = (int32_t)p;
   }
 }
 
@@ -255,29 +252,41 @@ __global__ void k_mlp_predict(const float* __restrict__ X, int64_t n, const __nv
 
 }  // namespace
 
-// contiguous item ranges of equal total cost, one per warp (bounds has parts + 1 entries)
-int nh_partition_items(const nh_oriented* o, const float* vertex_cost, int64_t parts, int64_t** bounds_out,
-                       cudaStream_t st) {
-  *bounds_out = nullptr;
+// items in decreasing estimated cost, for largest-first dynamic scheduling
+int nh_schedule_items(const nh_oriented* o, const float* vertex_cost, int32_t** order_out,
+                      unsigned long long** next_out, cudaStream_t st) {
+  *order_out = nullptr;
+  *next_out = nullptr;
   GView g = make_view(o, nullptr);
-  uint32_t* units = nullptr;
-  int64_t* prefix = nullptr;
-  int64_t* bounds = nullptr;
+  uint8_t* bucket = nullptr;
+  uint32_t* hist = nullptr;
+  int64_t* off = nullptr;
+  unsigned long long* cursor = nullptr;
+  int32_t* order = nullptr;
+  unsigned long long* next = nullptr;
   int rc = NH_OK;
-  if ((rc = nh_alloc(&units, o->m, st)) || (rc = nh_alloc(&prefix, o->m + 1, st)) || (rc = nh_alloc(&bounds, parts + 1, st))) {
-    nh_free(units, st); nh_free(prefix, st); nh_free(bounds, st);
+  if ((rc = nh_alloc(&bucket, o->m, st)) || (rc = nh_alloc(&hist, 32, st)) || (rc = nh_alloc(&off, 33, st)) ||
+      (rc = nh_alloc(&cursor, 32, st)) || (rc = nh_alloc(&order, o->m, st)) || (rc = nh_alloc(&next, 1, st))) {
+    nh_free(bucket, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(order, st); nh_free(next, st);
     return rc;
   }
-  k_item_units<<<nh_blocks_for(o->m, 256, 152 * 32), 256, 0, st>>>(g, vertex_cost, units);
+  cudaMemsetAsync(hist, 0, 32 * sizeof(uint32_t), st);
+  cudaMemsetAsync(cursor, 0, 32 * sizeof(unsigned long long), st);
+  cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+  k_item_bucket<<<nh_blocks_for(o->m, 256, 152 * 32), 256, 0, st>>>(g, vertex_cost, bucket, hist);
   nh_note_launch();
-  rc = nh_exclusive_scan_u32(units, prefix, o->m, st);
+  rc = nh_exclusive_scan_u32(hist, off, 32, st);
   if (!rc) {
-    k_bounds<<<nh_blocks_for(parts + 1, 256, 152 * 8), 256, 0, st>>>(prefix, o->m, parts, bounds);
+    k_item_scatter<<<nh_blocks_for(o->m, 256, 152 * 32), 256, 0, st>>>(o->m, bucket, off, cursor, order);
     nh_note_launch();
   }
-  nh_free(units, st); nh_free(prefix, st);
-  if (rc) { nh_free(bounds, st); return rc; }
-  *bounds_out = bounds;
+  nh_free(bucket, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st);
+  if (rc) {
+    nh_free(order, st); nh_free(next, st);
+    return rc;
+  }
+  *order_out = order;
+  *next_out = next;
   return NH_OK;
 }
 

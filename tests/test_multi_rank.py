@@ -1,0 +1,44 @@
+"""The multi-GPU form is independent replicas (the peel does not shard): the benchmark takes the
+slowest rank's time and counts every rank's units.  Checked with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = bench.reduce_max(100.0 + 50.0 * rank)  # rank 1 is the slower replica
+    out[rank] = (t, bench.whole_job_rate(1000, world, 2, t))
+    dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_count_every_rank():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    for rank in range(world):
+        t, v = out[rank]
+        assert t == 150.0
+        assert v == pytest.approx(2 * 1000 * 2 / 0.150)
+
+
+def test_single_rank_is_unchanged():
+    import bench
+    assert bench.reduce_max(42.0) == 42.0
+    assert bench.whole_job_rate(10, 1, 3, 1000.0) == pytest.approx(30.0)
