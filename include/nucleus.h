@@ -99,7 +99,8 @@ int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_
  * id in A decrements the other live members once and links the members of A in it; an
  * s-clique that died in an earlier round is linked from R to one of its earlier-peeled members
  * of least core (link_mode 0, the definition of §3) -- link_mode 1 instead links R with every
- * member peeled no later than R (the literal pair rule of Alg. 3).
+ * member peeled no later than R (the literal pair rule of Alg. 3); link_mode 2 computes the core
+ * numbers only (uf and L may be NULL), for nh_hierarchy_two_phase (§7.4).
  * Inputs: cnt uint32[n_r] (s-clique-degrees, not modified).
  * Outputs: core uint32[n_r] (exact (r,s)-clique core numbers), round uint32[n_r] (1-based peel
  * round), uf int32[n_r] and L int32[n_r] (the union-find and nearest-lower-core table of

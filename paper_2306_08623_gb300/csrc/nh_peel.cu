@@ -970,7 +970,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   if (ri->n_r == 0 && nh_supported(r, s)) return NH_OK;  // arrays may be empty (null)
   if (!cnt || !val || !round) return NH_ERR_INVALID;
   if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
-  if (exact && (!uf || !L || link_mode < 0 || link_mode > 1)) return NH_ERR_INVALID;
+  if (exact && (link_mode < 0 || link_mode > 2 || (link_mode < 2 && (!uf || !L)))) return NH_ERR_INVALID;
   if (!exact && !(delta > 0.0)) return NH_ERR_INVALID;
   const int64_t n_r = ri->n_r;
   if (stats) *stats = nh_peel_stats{};
@@ -1002,8 +1002,8 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   if (exact) {
     if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
       goto cleanup;
-    unsigned long long cap = 4096;
-    while (cap < 2ull * (unsigned long long)n_r && cap < (1ull << 24)) cap <<= 1;
+    unsigned long long cap = link_mode == 2 ? 1 : 4096;
+    while (link_mode != 2 && cap < 2ull * (unsigned long long)n_r && cap < (1ull << 24)) cap <<= 1;
     if ((rc = nh_alloc(&A.lk.cache, (int64_t)cap, st))) goto cleanup;
     A.lk.cache_mask = cap - 1;
     cudaMemsetAsync(A.lk.cache, 0xff, sizeof(unsigned long long) * cap, st);

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnucleus.so")
 
 SUPPORTED = ((1, 2), (1, 3), (2, 3), (2, 4), (3, 4))
-LINK_MODES = {"def": 0, "pair": 1}
+LINK_MODES = {"def": 0, "pair": 1, "none": 2}
 
 
 class NucleusError(RuntimeError):
@@ -173,6 +173,21 @@ def peel_and_link(o: Oriented, ri: RIndex, s: int, cnt: torch.Tensor, link_mode:
         o.handle, ri.handle, s, _dptr(cnt), _dptr(out["core"]), _dptr(out["round"]), _dptr(out["uf"]),
         _dptr(out["L"]), LINK_MODES[link_mode], ctypes.byref(st) if st is not None else None, _stream(stream)))
     res = {k: out[k][: ri.n_r] for k in ("core", "round", "uf", "L")}
+    if st is not None:
+        res["stats"] = st.as_dict()
+    return res
+
+
+def peel_cores(o: Oriented, ri: RIndex, s: int, cnt: torch.Tensor, stats: bool = False, stream=None) -> dict:
+    """The exact peel without linking (core numbers and round stamps only; link mode 2)."""
+    n = max(ri.n_r, 1)
+    core = torch.empty(n, dtype=torch.int32, device="cuda")
+    rnd = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = PeelStats() if stats else None
+    _check("nh_peel_and_link", lib().nh_peel_and_link(o.handle, ri.handle, s, _dptr(cnt), _dptr(core), _dptr(rnd),
+                                                      None, None, 2, ctypes.byref(st) if st is not None else None,
+                                                      _stream(stream)))
+    res = {"core": core[: ri.n_r], "round": rnd[: ri.n_r]}
     if st is not None:
         res["stats"] = st.as_dict()
     return res
@@ -356,14 +371,24 @@ def kernel_launches() -> int:
 
 
 def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: str = "def", stats: bool = False,
-              stream=None) -> dict:
+              method: str = "el", stream=None) -> dict:
     """The whole exact path on device tensors: orientation, r-clique index, s-clique counts, peel
-    with link-efficient, construct-tree."""
+    and hierarchy.  method "el": link-efficient interleaved with the peel, then construct-tree
+    (Alg. 3 + Alg. 5); "te": core numbers, then the two-phase hierarchy (§7.4, definitional
+    reading only); "auto": "el" for s - r = 1 and "te" otherwise (the paper's finding that the
+    two-phase form wins as s - r grows)."""
+    if method == "auto":
+        method = "el" if s - r == 1 or link_mode != "def" else "te"
     o = build_orientation(off, adj, stream)
     ri = index_r_cliques(o, r, stream)
     cnt, n_s = count_s_cliques(o, ri, s, stream=stream)
-    pk = peel_and_link(o, ri, s, cnt, link_mode=link_mode, stats=stats, stream=stream)
-    parent, label, nn = construct_tree(pk["core"], pk["uf"], pk["L"], stream=stream)
+    if method == "te":
+        assert link_mode == "def", "the two-phase hierarchy follows the definition"
+        pk = peel_cores(o, ri, s, cnt, stats=stats, stream=stream)
+        parent, label, nn = hierarchy_two_phase(o, ri, s, pk["core"], stream=stream)
+    else:
+        pk = peel_and_link(o, ri, s, cnt, link_mode=link_mode, stats=stats, stream=stream)
+        parent, label, nn = construct_tree(pk["core"], pk["uf"], pk["L"], stream=stream)
     res = {"oriented": o, "rindex": ri, "n_r": ri.n_r, "n_s": n_s, "cnt": cnt, "parent": parent,
            "label": label, "n_nodes": nn}
     res.update(pk)

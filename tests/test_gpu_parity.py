@@ -289,3 +289,23 @@ def test_two_phase_hierarchy(nc, r, s):
         ref = oracle.nucleus(off, adj, r, s)
         compare_hierarchy(parent.cpu().numpy(), u32(label), nn, ref["leaf_node"], ref["node_parent"],
                           ref["node_label"])
+
+
+@pytest.mark.parametrize("r,s", SUPPORTED)
+@pytest.mark.parametrize("method", ["te", "auto"])
+def test_hierarchy_methods(nc, r, s, method):
+    """The cores-only peel (link mode 2, no union-find) gives the same cores and round stamps as the
+    linking peel; the te/auto hierarchy from it equals the oracle's."""
+    for off, adj in [gg.rmat(11, 8, 5), gg.chung_lu(3000, 2.1, 10, 6, groups=6, per_group=5, size_lo=6, size_hi=14),
+                     gg.from_edges(4, []), gg.complete(6)]:
+        d_off, d_adj = to_dev(off, adj)
+        res = nc.hierarchy(d_off, d_adj, r, s, method=method, stats=True)
+        ref = oracle.nucleus(off, adj, r, s)
+        assert np.array_equal(u32(res["cnt"]), ref["cnt"])
+        assert np.array_equal(u32(res["core"]), ref["core"])
+        compare_hierarchy(res["parent"].cpu().numpy(), u32(res["label"]), res["n_nodes"], ref["leaf_node"],
+                          ref["node_parent"], ref["node_label"])
+        pk = nc.peel_cores(res["oriented"], res["rindex"], s, res["cnt"])
+        assert np.array_equal(u32(pk["core"]), ref["core"])
+        # the peel is round-synchronous, so its round stamps do not depend on linking
+        assert np.array_equal(u32(pk["round"]), u32(res["round"]))
