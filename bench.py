@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
+    ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
     ap.add_argument("--workload", choices=["rmat18", "cl4m", "batch512", "approx", "peel1"], default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
@@ -525,10 +526,11 @@ def run_peel1(args):
     d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
     for _ in range(2):
         a = _ev()
-        res = nc.hierarchy(d_off, d_adj, r, s, stats=True)
+        res = nc.hierarchy(d_off, d_adj, r, s, stats=True, method=args.method)
         b = _ev()
     line = {"metric": "exact hierarchy time", "value": _ms(a, b), "unit": "ms", "higher_is_better": False,
-            "config": {"workload": "R-MAT scale %d EF16 seed 2 (%d,%d)" % (args.scale, r, s), "n_r": res["n_r"],
+            "config": {"workload": "R-MAT scale %d EF16 seed 2 (%d,%d) method %s" % (args.scale, r, s, args.method),
+                       "n_r": res["n_r"],
                        "n_s": res["n_s"], "nodes": res["n_nodes"], "stats": res["stats"]}}
     print(json.dumps(line), flush=True)
 

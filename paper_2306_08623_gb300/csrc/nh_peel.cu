@@ -30,6 +30,7 @@ static int g_peel_max_group = 1024;  // set by nh_set_peel_max_group
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kTaskItems = 4096;  // largest frontier re-listed in work-proportional tasks
 constexpr int kLinkStack = 16;
 constexpr uint32_t kNone = 0xffffffffu;
 
@@ -58,6 +59,7 @@ struct PeelCtl {
   unsigned long long f_count;
   unsigned long long drain_n;
   unsigned long long ovf_count[2];
+  unsigned long long task_next;     // next re-listing task of the round (work-proportional mode)
   // statistics
   unsigned long long st_rounds, st_levels, st_listed, st_dec, st_link, st_unite, st_scan, st_probe, st_front,
       st_ovf;
@@ -90,6 +92,7 @@ struct PeelArgs {
   int link_mode;          // 0 definitional, 1 pairwise, -1 none
   int union_mode;         // two-phase hierarchy: re-listing unites instead of peeling
   int gmax;               // largest number of warps per frontier r-clique (power of two)
+  const uint32_t* cost;   // chunks of 32 list entries per r-clique (work-proportional re-listing)
   int32_t* touched;       // two-phase: roots joined at the current level
   unsigned long long* touched_n;
   unsigned long long touched_cap;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void ovf_push(const LinkEnv& E, int32_t a, int32_t b,
 
 // link-efficient(R0, Q0) of Alg. 5 with the recursion replaced by a small per-thread stack; calls
 // that do not fit go to the overflow queue, drained after the round.
-__device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& ls) {
+__device__ __noinline__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& ls) {
   int32_t sR[kLinkStack], sQ[kLinkStack];
   int sp = 0;
   sR[0] = R0; sQ[0] = Q0; sp = 1;
@@ -386,7 +389,7 @@ __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, in
 }
 
 // warp-collective
-__device__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane, LocalStats& ls) {
+__device__ __noinline__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane, LocalStats& ls) {
   __syncwarp();
   const int n = min(*(volatile int*)W.cnt, kLinkBuf);
   if (n == 0) return;
@@ -515,10 +518,58 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 // re-listing of one frontier r-clique by one warp
 // ---------------------------------------------------------------------------------------------
 
+// Length of the list whose 32-entry chunks the re-listing of r-clique Rid walks: the adjacency
+// list of its vertex of least degree, or for (3,4) the shortest triangle list of its three edges.
+template <int R, int S>
+__device__ __forceinline__ int64_t relist_len(const GView& g, int32_t Rid) {
+  if constexpr (R == 1) {
+    return __ldg(g.off + Rid + 1) - __ldg(g.off + Rid);
+  } else if constexpr (R == 2) {
+    const int32_t u = __ldg(g.eu + Rid), v = __ldg(g.ev + Rid);
+    const int64_t du = __ldg(g.off + u + 1) - __ldg(g.off + u), dv = __ldg(g.off + v + 1) - __ldg(g.off + v);
+    return du < dv ? du : dv;
+  } else {
+    const int32_t v0 = __ldg(g.tri + 3 * (int64_t)Rid), v1 = __ldg(g.tri + 3 * (int64_t)Rid + 1),
+                  v2 = __ldg(g.tri + 3 * (int64_t)Rid + 2);
+    if constexpr (S == 4) {
+      const int64_t e[3] = {nh_edge_id(g, v0, v1), nh_edge_id(g, v0, v2), nh_edge_id(g, v1, v2)};
+      int64_t m = INT64_MAX;
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        const int64_t len = e[i] < 0 ? 0 : __ldg(g.etoff + e[i] + 1) - __ldg(g.etoff + e[i]);
+        m = len < m ? len : m;
+      }
+      return m;
+    } else {
+      int64_t m = INT64_MAX;
+      const int32_t vv[3] = {v0, v1, v2};
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        const int64_t len = __ldg(g.off + vv[i] + 1) - __ldg(g.off + vv[i]);
+        m = len < m ? len : m;
+      }
+      return m;
+    }
+  }
+}
+
+// chunks of 32 list entries per r-clique, the unit of work-proportional re-listing
+template <int R, int S>
+__global__ void k_chunk_cost(GView g, int64_t n_r, uint32_t* __restrict__ cost) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = (relist_len<R, S>(g, (int32_t)i) + 31) >> 5;
+    cost[i] = c > 0xffffffffll ? 0xffffffffu : (uint32_t)c;
+  }
+}
+
+// Re-lists the s-cliques of r-clique Rid found from chunks c0, c0 + cstep, ... (< cend) of its
+// list (chunk c = entries [32c, 32c + 32)).  For s - r = 2 the out-lists of the candidates found
+// in a chunk are split over Ge callers: this one expands candidates of lane index = se mod Ge.
+// The caller brackets the calls for one Rid with wl_begin / wl_flush (exact peel).
 template <int R, int S, bool EXACT>
-__device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
-                            int sub, int G, const WarpLinks& W, LocalStats& ls) {
-  if constexpr (EXACT) wl_begin(W, lane);
+__device__ __noinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
+                            int64_t c0, int64_t cstep, int64_t cend, int Ge, int se, const WarpLinks& W,
+                            LocalStats& ls) {
   constexpr int kPerLane = (S - R == 1) ? R : 5;  // link targets one lane can add per converged step
   const GView& g = A.g;
   int32_t vx[3] = {0, 0, 0};
@@ -555,9 +606,9 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
     int bt = 0;
     if (th[1] - tl[1] < th[bt] - tl[bt]) bt = 1;
     if (th[2] - tl[2] < th[bt] - tl[bt]) bt = 2;
-    if (lane == 0 && sub == 0) ls.scan += (unsigned long long)(th[bt] - tl[bt]);
-    for (int64_t base = tl[bt] + 32 * sub; base < th[bt]; base += 32 * G) {
-      const int64_t j = base + lane;
+    if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(th[bt] - tl[bt]);
+    for (int64_t c = c0; c < cend && tl[bt] + 32 * c < th[bt]; c += cstep) {
+      const int64_t j = tl[bt] + 32 * c + lane;
       bool ok = j < th[bt];
       int32_t mem[3] = {0, 0, 0};
       if (ok) {
@@ -576,7 +627,6 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
       if (ok) process_S<3, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
       if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
     }
-    if constexpr (EXACT) wl_flush(W, A, Rid, lane, ls);
     return;
   }
   int64_t lo[3], hi[3];
@@ -590,14 +640,9 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
   for (int i = 1; i < R; i++)
     if (hi[i] - lo[i] < hi[best] - lo[best]) best = i;
   const int64_t b0 = lo[best], b1 = hi[best];
-  if (lane == 0 && sub == 0) ls.scan += (unsigned long long)(b1 - b0);
-  // s - r = 2: the G warps of the group form Gc chunk-groups of Ge warps; the Ge warps of one
-  // chunk-group scan the same 32 candidates and each expands the out-lists of every Ge-th of
-  // them, so that the expansion of one heavy candidate chunk is spread over Ge warps too
-  const int Ge = (S - R == 2) ? (G < 32 ? G : 32) : 1;
-  const int Gc = G / Ge, sc = sub / Ge, se = sub % Ge;
-  for (int64_t base = b0 + 32 * sc; base < b1; base += 32 * Gc) {
-    const int64_t j = base + lane;
+  if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(b1 - b0);
+  for (int64_t c = c0; c < cend && b0 + 32 * c < b1; c += cstep) {
+    const int64_t j = b0 + 32 * c + lane;
     bool ok = j < b1;
     int32_t w = 0;
     int32_t ew[3] = {0, 0, 0};
@@ -683,7 +728,99 @@ __device__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t
     }
     if constexpr (EXACT && S - R == 1) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
   }
+}
+
+// One r-clique re-listed by a group of G warps (this one is number sub): the warps take
+// interleaved chunks; for s - r = 2 they form G / Ge chunk-groups of Ge warps, the Ge warps of
+// one chunk-group scanning the same 32 candidates and each expanding the out-lists of every
+// Ge-th of them, so that the expansion of one heavy chunk is spread over Ge warps too.
+template <int R, int S, bool EXACT>
+__device__ __forceinline__ void relist_group(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf,
+                                             int lane, int sub, int G, const WarpLinks& W, LocalStats& ls) {
+  const int Ge = (S - R == 2) ? (G < 32 ? G : 32) : 1;
+  const int Gc = G / Ge, sc = sub / Ge, se = sub % Ge;
+  if constexpr (EXACT) wl_begin(W, lane);
+  relist_item<R, S, EXACT>(A, Rid, t, thr, nf, lane, sc, Gc, INT64_MAX, Ge, se, W, ls);
   if constexpr (EXACT) wl_flush(W, A, Rid, lane, ls);
+}
+
+// A list of at most kTaskItems r-cliques is cut into tasks of one 32-entry chunk each (for
+// s - r = 2: one Ge-th of a chunk's out-list expansions), which warps take from a shared counter,
+// so that a round lasts about its total work over the grid rather than its heaviest r-clique.
+// Every block builds the prefix sums of the chunk counts itself.  Block-collective; returns false
+// (having done nothing) when the chunk total does not fit 31 bits.
+template <int R, int S, bool EXACT>
+__device__ bool relist_tasks(const PeelArgs& A, const int32_t* items, unsigned int n, uint32_t t, uint32_t thr,
+                             int32_t* nf, int lane, long long nwarps, const WarpLinks& W, LocalStats& ls,
+                             uint32_t* s_pref, unsigned long long* s_wsum, unsigned long long* task_next) {
+  constexpr int kPer = kTaskItems / kThreads;
+  const unsigned int b = threadIdx.x * kPer;
+  uint32_t v[kPer];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    v[j] = (b + j < n) ? __ldg(A.cost + __ldcg(items + b + j)) : 0u;
+    sum += v[j];
+  }
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(NH_FULL, incl, d);
+    if (lane >= d) incl += o;
+  }
+  __syncthreads();  // the previous call's readers of s_pref / s_wsum are done
+  if (lane == 31) s_wsum[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  unsigned long long base = incl - sum, total = 0;
+  for (int w = 0; w < kThreads / 32; w++) {
+    const unsigned long long x = s_wsum[w];
+    if (w < (int)(threadIdx.x >> 5)) base += x;
+    total += x;
+  }
+  if (total >= (1ull << 31)) return false;
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    base += v[j];
+    if (b + j < n) s_pref[b + j] = (uint32_t)base;
+  }
+  __syncthreads();
+  int Ge = 1;
+  if constexpr (S - R == 2)
+    while (Ge < 32 && total * (unsigned long long)(2 * Ge) <= 4ull * (unsigned long long)nwarps) Ge *= 2;
+  const unsigned long long ntask = total * (unsigned long long)Ge;
+  const unsigned long long per = ntask / ((unsigned long long)nwarps * 8ull);
+  const unsigned long long bt = per > 0 ? per : 1ull;
+  int32_t curR = -1;
+  for (;;) {
+    unsigned long long k0 = 0;
+    if (lane == 0) k0 = atomicAdd(task_next, bt);
+    k0 = __shfl_sync(NH_FULL, k0, 0);
+    if (k0 >= ntask) break;
+    const unsigned long long k1 = k0 + bt < ntask ? k0 + bt : ntask;
+    for (unsigned long long k = k0; k < k1; k++) {
+      const uint32_t kc = (uint32_t)(k / (unsigned long long)Ge);
+      const int se = (int)(k % (unsigned long long)Ge);
+      unsigned int lo = 0, hi = n;  // first item whose inclusive prefix exceeds kc
+      while (lo < hi) {
+        const unsigned int mid = (lo + hi) >> 1;
+        if (s_pref[mid] <= kc) lo = mid + 1; else hi = mid;
+      }
+      const uint32_t cl = kc - (lo ? s_pref[lo - 1] : 0u);
+      const int32_t Rid = __ldcg(items + lo);
+      if (Rid != curR) {
+        if constexpr (EXACT) {
+          if (curR >= 0) wl_flush(W, A, curR, lane, ls);
+          wl_begin(W, lane);
+        }
+        curR = Rid;
+      }
+      relist_item<R, S, EXACT>(A, Rid, t, thr, nf, lane, cl, 1, (int64_t)cl + 1, Ge, se, W, ls);
+    }
+  }
+  if constexpr (EXACT) {
+    if (curR >= 0) wl_flush(W, A, curR, lane, ls);
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -714,6 +851,7 @@ __device__ void leader_after_scan(const PeelArgs& A) {
 template <bool EXACT>
 __device__ void leader_end_of_round(const PeelArgs& A) {
   PeelCtl* c = A.lk.ctl;
+  c->task_next = 0;
   const unsigned int oc = c->ovf_cur;
   if (c->ovf_count[oc] > 0) {
     c->draining = 1;
@@ -764,6 +902,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
   __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
   __shared__ int s_lcnt[kThreads / 32];
   __shared__ int32_t s_seen[kThreads / 32][kSeen];
+  __shared__ uint32_t s_pref[kTaskItems];
+  __shared__ unsigned long long s_wsum[kThreads / 32];
   if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
   const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
@@ -831,16 +971,20 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
       const unsigned long long fs = vc->fsize;
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
-      // a small frontier gets several warps per r-clique (G, a power of two up to 1024); the
-      // warps of a group take interleaved 32-entry chunks of the scanned list
-      int G = 1;
-      while (G < A.gmax && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
-      const long long ngroups = nwarps / G;
-      const long long grp = gwarp / G;
-      const int sub = (int)(gwarp % G);
-      if (grp < ngroups) {
-        for (unsigned long long it = (unsigned long long)grp; it < fs; it += (unsigned long long)ngroups)
-          relist_item<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, sub, G, W, ls);
+      const bool tasks = fs <= (unsigned long long)kTaskItems &&
+                         relist_tasks<R, S, EXACT>(A, fr, (unsigned int)fs, t, thr, nf, lane, nwarps, W, ls, s_pref,
+                                                   s_wsum, &ctl->task_next);
+      if (!tasks) {
+        // a small frontier gets several warps per r-clique (G, a power of two up to 1024)
+        int G = 1;
+        while (G < A.gmax && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
+        const long long ngroups = nwarps / G;
+        const long long grp = gwarp / G;
+        const int sub = (int)(gwarp % G);
+        if (grp < ngroups) {
+          for (unsigned long long it = (unsigned long long)grp; it < fs; it += (unsigned long long)ngroups)
+            relist_group<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, sub, G, W, ls);
+        }
       }
     }
     // end of round: drain deferred link calls, then advance
@@ -960,6 +1104,16 @@ int dispatch(int r, int s, PeelArgs& A, cudaStream_t st) {
   return NH_ERR_UNSUPPORTED;
 }
 
+int launch_chunk_cost(int r, int s, const GView& g, int64_t n_r, uint32_t* cost, cudaStream_t st) {
+  const unsigned blocks = nh_blocks_for(n_r, 256, 152 * 16);
+  if (r == 1) k_chunk_cost<1, 2><<<blocks, 256, 0, st>>>(g, n_r, cost);
+  else if (r == 2) k_chunk_cost<2, 3><<<blocks, 256, 0, st>>>(g, n_r, cost);
+  else if (r == 3 && s == 4) k_chunk_cost<3, 4><<<blocks, 256, 0, st>>>(g, n_r, cost);
+  else return NH_ERR_UNSUPPORTED;
+  nh_note_launch();
+  return NH_OK;
+}
+
 // shared driver for the exact and the approximate peel
 int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* val,
              uint32_t* round, int32_t* uf, int32_t* L, int link_mode, double delta, nh_peel_stats* stats,
@@ -993,12 +1147,16 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   int rc = NH_OK;
   uint32_t* thr_dev = nullptr;
   unsigned int* dmax = nullptr;
+  uint32_t* cost = nullptr;
   std::vector<uint32_t> thr_host;
   if ((rc = nh_alloc(&A.cnt, n_r, st)) || (rc = nh_alloc(&A.alive[0], n_r, st)) ||
       (rc = nh_alloc(&A.alive[1], n_r, st)) || (rc = nh_alloc(&A.front[0], n_r, st)) ||
-      (rc = nh_alloc(&A.front[1], n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st))) {
+      (rc = nh_alloc(&A.front[1], n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) ||
+      (rc = nh_alloc(&cost, n_r, st))) {
     goto cleanup;
   }
+  if ((rc = launch_chunk_cost(r, s, A.g, n_r, cost, st))) goto cleanup;
+  A.cost = cost;
   if (exact) {
     if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
       goto cleanup;
@@ -1068,7 +1226,7 @@ cleanup:
   nh_free(A.cnt, st); nh_free(A.alive[0], st); nh_free(A.alive[1], st); nh_free(A.front[0], st);
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
   nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
-  nh_free(thr_dev, st); nh_free(dmax, st);
+  nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }
@@ -1158,6 +1316,8 @@ __global__ void __launch_bounds__(kThreads) k_two_phase(PeelArgs A, TreeOut T) {
   __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
   __shared__ int s_lcnt[kThreads / 32];
   __shared__ int32_t s_seen[kThreads / 32][kSeen];
+  __shared__ uint32_t s_pref[kTaskItems];
+  __shared__ unsigned long long s_wsum[kThreads / 32];
   if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
   const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
@@ -1167,16 +1327,19 @@ __global__ void __launch_bounds__(kThreads) k_two_phase(PeelArgs A, TreeOut T) {
     const unsigned long long cnt = (unsigned long long)(hi - lo);
     if (cnt == 0) continue;
     // unions at this level
-    {
+    const bool tasks = cnt <= (unsigned long long)kTaskItems &&
+                       relist_tasks<R, S, true>(A, T.order + lo, (unsigned int)cnt, 0u, level, nullptr, lane,
+                                                nwarps, W, ls, s_pref, s_wsum, &ctl->task_next);
+    if (!tasks) {
       int G = 1;
       while (G < A.gmax && (unsigned long long)(2 * G) * cnt <= (unsigned long long)nwarps) G *= 2;
       const long long ngroups = nwarps / G, grp = gwarp / G;
       const int sub = (int)(gwarp % G);
       if (grp < ngroups)
         for (unsigned long long it = (unsigned long long)grp; it < cnt; it += (unsigned long long)ngroups)
-          relist_item<R, S, true>(A, T.order[lo + it], 0u, level, nullptr, lane, sub, G, W, ls);
+          relist_group<R, S, true>(A, T.order[lo + it], 0u, level, nullptr, lane, sub, G, W, ls);
     }
-    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
+    if (!grid_sync(ctl, A.timeout_ns, [&] { ctl->task_next = 0; })) break;
     // a node for every component holding an r-clique of this level
     for (long long i = gtid; i < (long long)cnt; i += nthreads) {
       const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
@@ -1289,13 +1452,16 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   int64_t* off = nullptr;
   unsigned long long* cursor = nullptr;
   int32_t* order = nullptr;
+  uint32_t* cost = nullptr;
   int rc = NH_OK;
   unsigned int kmax = 0;
   if ((rc = nh_alloc(&A.lk.uf, n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) || (rc = nh_alloc(&A.touched, (int64_t)A.touched_cap, st)) ||
       (rc = nh_alloc(&A.touched_n, 1, st)) || (rc = nh_alloc(&T.lvl, n_r, st)) || (rc = nh_alloc(&T.nid, n_r, st)) ||
       (rc = nh_alloc(&T.top, n_r, st)) || (rc = nh_alloc(&T.node_count, 1, st)) || (rc = nh_alloc(&dmax, 1, st)) ||
-      (rc = nh_alloc(&order, n_r, st)))
+      (rc = nh_alloc(&order, n_r, st)) || (rc = nh_alloc(&cost, n_r, st)))
     goto cleanup;
+  if ((rc = launch_chunk_cost(r, s, A.g, n_r, cost, st))) goto cleanup;
+  A.cost = cost;
   cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
   k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, core, dmax);
   nh_note_launch();
@@ -1339,7 +1505,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
 cleanup:
   nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
   nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
-  nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st);
+  nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(cost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }
