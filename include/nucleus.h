@@ -217,6 +217,14 @@ int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int
  * warps also repeat walks.  g: power of two in [1, 1024].  Results never depend on it. */
 int nh_set_peel_max_group(int g);
 
+/* Tuning knob of the peel and two-phase kernels (process-wide): a frontier (or level) of at most
+ * n r-clique ids is cut into tasks of one 32-entry chunk of a re-listed list each, which warps
+ * take from a shared counter; larger ones get warp groups as above.  0 turns the task form off;
+ * -1 (the default) is automatic: 4096, except 0 for the linking peel (link modes 0, 1) with
+ * s - r = 1, where one r-clique's link targets spread over many warps repeat walks.
+ * n in [-1, 4096]; NH_ERR_INVALID otherwise.  Results never depend on it. */
+int nh_set_peel_task_items(int n);
+
 /* number of CUDA kernels this library has launched in the process so far (host counter) */
 int64_t nh_kernel_launches(void);
 

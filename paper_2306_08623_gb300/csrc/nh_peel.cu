@@ -23,1000 +23,12 @@
 #include <cmath>
 #include <vector>
 
-#include "nh_internal.cuh"
+#include "nh_peel.cuh"
 
-static int g_peel_max_group = 1024;  // set by nh_set_peel_max_group
+static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
+static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
 
-namespace {
-
-constexpr int kThreads = 256;
-constexpr int kTaskItems = 4096;  // largest frontier re-listed in work-proportional tasks
-constexpr int kLinkStack = 16;
-constexpr uint32_t kNone = 0xffffffffu;
-
-struct PeelCtl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  int err;
-  int done;
-  unsigned int t;
-  unsigned int thr;
-  unsigned int bucket;
-  unsigned int rounds_in_bucket;
-  unsigned int need_scan;
-  unsigned int cur;
-  unsigned int alive_cur;
-  unsigned int gmin;
-  unsigned int draining;
-  unsigned int drain_buf;
-  unsigned int ovf_cur;
-  unsigned int kmax;
-  unsigned long long finished;
-  unsigned long long fsize;
-  unsigned long long nf_count;
-  unsigned long long alive_n;
-  unsigned long long alive2_count;
-  unsigned long long f_count;
-  unsigned long long drain_n;
-  unsigned long long ovf_count[2];
-  unsigned long long task_next;     // next re-listing task of the round (work-proportional mode)
-  // statistics
-  unsigned long long st_rounds, st_levels, st_listed, st_dec, st_link, st_unite, st_scan, st_probe, st_front,
-      st_ovf;
-};
-
-struct LinkEnv {
-  int32_t* uf;
-  int32_t* L;
-  const uint32_t* core;
-  int32_t* J;                       // jump pointers (may be null)
-  unsigned long long* cache;        // lossy set of linked root pairs (may be null)
-  unsigned long long cache_mask;
-  int2* ovf[2];
-  unsigned long long ovf_cap;
-  PeelCtl* ctl;
-};
-
-struct PeelArgs {
-  GView g;
-  int64_t n_r;
-  uint32_t* cnt;          // working counts
-  const uint32_t* cnt0;   // s-clique-degrees
-  uint32_t* val;          // core (exact) or approximate value
-  uint32_t* round;
-  int32_t* alive[2];
-  int32_t* front[2];
-  const uint32_t* thresholds;
-  int n_thr;
-  uint32_t T;
-  int link_mode;          // 0 definitional, 1 pairwise, -1 none
-  int union_mode;         // two-phase hierarchy: re-listing unites instead of peeling
-  int gmax;               // largest number of warps per frontier r-clique (power of two)
-  const uint32_t* cost;   // chunks of 32 list entries per r-clique (work-proportional re-listing)
-  int32_t* touched;       // two-phase: roots joined at the current level
-  unsigned long long* touched_n;
-  unsigned long long touched_cap;
-  int stats;
-  unsigned long long timeout_ns;
-  LinkEnv lk;
-};
-
-struct LocalStats {
-  unsigned long long listed, dec, link, unite, scan, probe, ovf;
-};
-
-// ---------------------------------------------------------------------------------------------
-// warp helpers
-// ---------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = min(v, __shfl_xor_sync(NH_FULL, v, d));
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(NH_FULL, v, d);
-  return v;
-}
-
-// warp-aggregated append; every lane of the warp must call it
-__device__ __forceinline__ unsigned long long warp_append(unsigned long long* counter, bool pred, int lane) {
-  const unsigned m = __ballot_sync(NH_FULL, pred);
-  if (!m) return 0;
-  const int leader = __ffs(m) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
-  base = __shfl_sync(NH_FULL, base, leader);
-  return base + __popc(m & ((1u << lane) - 1u));
-}
-
-// Grid barrier with a bounded wait.  The last block to arrive runs `leader` (thread 0) before
-// releasing the others.  Returns false once any block has recorded an error.
-template <class F>
-__device__ __forceinline__ bool grid_sync(PeelCtl* ctl, unsigned long long timeout_ns, F leader) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile PeelCtl* vc = ctl;
-    const unsigned int gen = vc->bar_gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      __threadfence();
-      leader();
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = nh_globaltimer();
-      while (vc->bar_gen == gen) {
-        __nanosleep(64);
-        if (nh_globaltimer() - t0 > timeout_ns) {
-          atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = (vc->err == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// ---------------------------------------------------------------------------------------------
-// concurrent union-find (CAS, path halving) and link-efficient (Alg. 5)
-// ---------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ int32_t uf_find(int32_t* uf, int32_t x) {
-  // parent ids strictly decrease along a path, so this ends; the cap is only a guard
-  for (int it = 0; it < (1 << 24); ++it) {
-    const int32_t p = __ldcg(uf + x);
-    if (p == x) return x;
-    const int32_t gp = __ldcg(uf + p);
-    if (gp != p) atomicCAS(uf + x, p, gp);
-    x = gp;
-  }
-  return x;
-}
-
-// unite the sets of a and b: the root of larger id is hung under the root of smaller id.
-// Returns the root that was hung (it is this caller's job to pass on its L entry), or -1 when
-// a and b were already in one set.
-__device__ __forceinline__ int32_t uf_unite(int32_t* uf, int32_t a, int32_t b, PeelCtl* ctl) {
-  for (int it = 0; it < (1 << 20); ++it) {
-    a = uf_find(uf, a);
-    b = uf_find(uf, b);
-    if (a == b) return -1;
-    if (a < b) { const int32_t t = a; a = b; b = t; }
-    if (atomicCAS(uf + a, a, b) == a) {
-      __threadfence();
-      return a;
-    }
-  }
-  atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
-  return -1;
-}
-
-__device__ __forceinline__ void ovf_push(const LinkEnv& E, int32_t a, int32_t b, LocalStats& ls) {
-  const unsigned int cur = *(volatile unsigned int*)&E.ctl->ovf_cur;
-  const unsigned long long pos = atomicAdd(&E.ctl->ovf_count[cur], 1ull);
-  if (pos < E.ovf_cap) E.ovf[cur][pos] = make_int2(a, b);
-  else atomicCAS(&E.ctl->err, 0, NH_ERR_OVERFLOW);
-  ls.ovf++;
-}
-
-// link-efficient(R0, Q0) of Alg. 5 with the recursion replaced by a small per-thread stack; calls
-// that do not fit go to the overflow queue, drained after the round.
-__device__ __noinline__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalStats& ls) {
-  int32_t sR[kLinkStack], sQ[kLinkStack];
-  int sp = 0;
-  sR[0] = R0; sQ[0] = Q0; sp = 1;
-  auto push = [&](int32_t a, int32_t b) {
-    if (a < 0 || b < 0) return;
-    if (sp < kLinkStack) { sR[sp] = a; sQ[sp] = b; ++sp; }
-    else ovf_push(E, a, b, ls);
-  };
-  unsigned int guard = 0;
-  while (sp > 0) {
-    if (++guard > (1u << 22)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
-    --sp;
-    int32_t R = sR[sp], Q = sQ[sp];
-    if (R < 0 || Q < 0) continue;
-    ls.link++;
-    uint32_t nR = __ldcg(E.core + R), nQ = __ldcg(E.core + Q);
-    if (nQ < nR) {
-      const int32_t t = R; R = Q; Q = t;
-      const uint32_t u = nR; nR = nQ; nQ = u;
-    }
-    R = uf_find(E.uf, R);
-    Q = uf_find(E.uf, Q);
-    if (R == Q) continue;
-    if (E.cache) {
-      // a pair of roots already linked states nothing new (components only grow)
-      const unsigned long long key = ((unsigned long long)(uint32_t)R << 32) | (uint32_t)Q;
-      unsigned long long* slot = E.cache + (nh_mix64(key) & E.cache_mask);
-      if (__ldcg(slot) == key) continue;
-      *slot = key;
-    }
-    if (nR == nQ) {
-      // Alg. 5 passes on L of whichever of R, Q stopped being a root.  Concurrently the roots
-      // actually joined may be others (R or Q may have been hung meanwhile), so the thread whose
-      // CAS hung a root passes on that root's L -- every hung root is handled exactly by the
-      // thread that hung it.
-      const int32_t child = uf_unite(E.uf, R, Q, E.ctl);
-      if (child >= 0) {
-        ls.unite++;
-        push(__ldcg(E.L + child), uf_find(E.uf, child));
-      }
-      continue;
-    }
-    // nR < nQ.  L[Q] is read only after Q is re-found as a root, and the value that was tested is
-    // the one passed on: with concurrent unites, a value read from a component that has just
-    // stopped being a root (or re-read after the test) could drop the fact "R meets Q at level
-    // nR" -- the sequential order of the paper's loop does not survive concurrency otherwise.
-    //
-    // The walk down Q's chain (Alg. 5's call link(R, L[Q]) when ND[L[Q]] > ND[R]) continues in
-    // place.  Jump pointers shorten it: J[C] is a component known to meet C at level core(J[C]) <
-    // core(C) (every component on C's chain qualifies, and the relation only ever grows), so for
-    // core(J[C]) >= nR the call link(R, C) states exactly what link(R, J[C]) states, and no
-    // component between C and J[C] (all of core > core(J[C])) is where R belongs.  Each walk
-    // records the deepest component it passed above level nR as the jump pointer of its start.
-    const int32_t Q0 = Q;
-    int32_t deepest = -1;
-    uint32_t c_deepest = 0;
-    for (unsigned int spin = 0;; ++spin) {
-      if (spin > (1u << 20)) { atomicCAS(&E.ctl->err, 0, NH_ERR_TIMEOUT); return; }
-      Q = uf_find(E.uf, Q);
-      if (E.J) {
-        const int32_t jq = __ldcg(E.J + Q);
-        if (jq >= 0) {
-          const uint32_t cj = __ldcg(E.core + jq);
-          if (cj > nR) {
-            deepest = jq;
-            c_deepest = cj;
-            Q = jq;
-            ++ls.link;
-            continue;
-          }
-          if (cj == nR) {
-            push(R, jq);
-            break;
-          }
-        }
-      }
-      const int32_t LQ = __ldcg(E.L + Q);
-      if (LQ < 0) {
-        if (atomicCAS(E.L + Q, -1, R) == -1) {
-          __threadfence();
-          const int32_t pQ = uf_find(E.uf, Q);
-          if (pQ != Q) push(R, pQ);
-          break;
-        }
-        continue;  // L[Q] was set meanwhile: retry with its value
-      }
-      const uint32_t cL = __ldcg(E.core + LQ);
-      if (cL < nR) {
-        if (atomicCAS(E.L + Q, LQ, R) == LQ) {
-          __threadfence();
-          const int32_t pQ = uf_find(E.uf, Q);
-          if (pQ != Q) push(R, pQ);
-          push(R, LQ);
-          break;
-        }
-        continue;
-      }
-      if (cL == nR) {
-        push(R, LQ);
-        break;
-      }
-      deepest = LQ;  // ND[L[Q]] > ND[R]: continue the walk from L[Q]
-      c_deepest = cL;
-      Q = LQ;
-      ++ls.link;
-    }
-    if (E.J && deepest >= 0) {
-      const int32_t j0 = __ldcg(E.J + Q0);
-      if (j0 < 0 || c_deepest < __ldcg(E.core + j0)) E.J[Q0] = deepest;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// per (R, S) step
-// ---------------------------------------------------------------------------------------------
-
-template <bool EXACT>
-__device__ __forceinline__ void dec(const PeelArgs& A, int32_t x, uint32_t t, uint32_t thr, int32_t* nf,
-                                    LocalStats& ls) {
-  const uint32_t old = atomicSub(A.cnt + x, 1u);
-  ls.dec++;
-  if (old == thr + 1u) {
-    const unsigned long long pos = atomicAdd(&A.lk.ctl->nf_count, 1ull);
-    nf[pos] = x;
-    __stcg(A.round + x, t + 1u);
-    __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
-  }
-}
-
-__device__ __forceinline__ int32_t tri_id(const PeelArgs& A, unsigned long long key, LocalStats& ls) {
-  ls.probe++;
-  const int64_t id = nh_tri_lookup(A.g.table, A.g.mask, key);
-  if (id < 0) {
-    atomicCAS(&A.lk.ctl->err, 0, NH_ERR_INTERNAL);
-    return 0;
-  }
-  return (int32_t)id;
-}
-
-// ---------------------------------------------------------------------------------------------
-// per-warp link buffer: the link targets of one frontier r-clique R are collected, replaced by
-// their union-find roots, sorted by decreasing core and de-duplicated, then linked as a chain
-// R - t1 - t2 - ... (t_i = targets in that order).  Since R meets t_i at level core(t_i) and
-// core(t_{i-1}) >= core(t_i), "t_{i-1} meets t_i at level core(t_i)" states the same
-// connectivity as "R meets t_i at core(t_i)", while link-efficient walks only between adjacent
-// levels instead of from R's level down to each target's level.
-// ---------------------------------------------------------------------------------------------
-
-constexpr int kLinkBuf = 256;
-
-struct WarpLinks {
-  unsigned long long* buf;
-  int* cnt;
-  int32_t* seen;  // kSeen roots this warp has already chained from the current R (direct-mapped)
-};
-
-constexpr int kSeen = 64;
-
-// warp-collective: forget the roots seen for the previous frontier r-clique
-__device__ __forceinline__ void wl_begin(const WarpLinks& W, int lane) {
-  __syncwarp();
-  for (int i = lane; i < kSeen; i += 32) W.seen[i] = -1;
-  __syncwarp();
-}
-
-__device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int32_t m,
-                                       LocalStats& ls) {
-  // a target whose component this warp has already chained from R adds nothing: R meets that
-  // whole component at its level already (a root that changed since only misses the filter)
-  const int32_t rt = uf_find(A.lk.uf, m);
-  if (W.seen[rt & (kSeen - 1)] == rt) return;
-  const int pos = atomicAdd(W.cnt, 1);
-  if (pos < kLinkBuf) W.buf[pos] = (unsigned long long)(uint32_t)m;
-  else link_run(A.lk, Rid, m, ls);  // buffer full (cannot happen with the flush policy): link directly
-}
-
-// warp-collective
-__device__ __noinline__ void wl_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane, LocalStats& ls) {
-  __syncwarp();
-  const int n = min(*(volatile int*)W.cnt, kLinkBuf);
-  if (n == 0) return;
-  int P = 2;  // sort only the smallest power of two holding the n entries
-  while (P < n) P <<= 1;
-  for (int i = lane; i < P; i += 32) {
-    unsigned long long key = ~0ull;
-    if (i < n) {
-      const int32_t rt = uf_find(A.lk.uf, (int32_t)W.buf[i]);
-      const uint32_t c = __ldcg(A.val + rt);
-      key = ((unsigned long long)(~c) << 32) | (uint32_t)rt;
-    }
-    W.buf[i] = key;
-  }
-  __syncwarp();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < P; i += 32) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long a = W.buf[i], b = W.buf[ixj];
-          if ((a > b) == ((i & k) == 0)) {
-            W.buf[i] = b;
-            W.buf[ixj] = a;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-  for (int i = lane; i < n; i += 32) {
-    const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
-    const int32_t prev = (i == 0) ? Rid : (int32_t)(W.buf[i - 1] & 0xffffffffull);
-    if (i > 0 && prev == cur) continue;
-    link_run(A.lk, prev, cur, ls);
-  }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) {  // record after every link of the chain has completed
-    const int32_t cur = (int32_t)(W.buf[i] & 0xffffffffull);
-    W.seen[cur & (kSeen - 1)] = cur;
-  }
-  __syncwarp();
-  if (lane == 0) *W.cnt = 0;
-  __syncwarp();
-}
-
-// flush when another step of 32 lanes could overflow the buffer (warp-collective)
-__device__ __forceinline__ void wl_maybe_flush(const WarpLinks& W, const PeelArgs& A, int32_t Rid, int lane,
-                                               int per_lane, LocalStats& ls) {
-  __syncwarp();
-  if (*(volatile int*)W.cnt > kLinkBuf - 32 * per_lane) wl_flush(W, A, Rid, lane, ls);
-}
-
-template <int CM, bool EXACT>
-__device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM], uint32_t t,
-                                          uint32_t thr, int32_t* nf, const WarpLinks& W, LocalStats& ls) {
-  if (A.union_mode) {
-    // two-phase hierarchy at level thr (= core of Rid): an s-clique whose least member core is
-    // thr joins all its members; its member of least id among those of core thr does it
-    int32_t attr = Rid;
-#pragma unroll
-    for (int j = 0; j < CM; j++) {
-      const uint32_t c = __ldcg(A.val + mem[j]);
-      if (c < thr) return;
-      if (c == thr && mem[j] < attr) attr = mem[j];
-    }
-    ls.listed++;
-    if (attr != Rid) return;
-#pragma unroll
-    for (int j = 0; j < CM; j++) {
-      const int32_t child = uf_unite(A.lk.uf, Rid, mem[j], A.lk.ctl);
-      if (child >= 0) {
-        ls.unite++;
-        const unsigned long long pos = atomicAdd(A.touched_n, 2ull);
-        if (pos + 1 < A.touched_cap) {
-          A.touched[pos] = child;
-          A.touched[pos + 1] = uf_find(A.lk.uf, child);
-        } else {
-          atomicCAS(&A.lk.ctl->err, 0, NH_ERR_OVERFLOW);
-        }
-      }
-    }
-    return;
-  }
-  uint32_t rd[CM];
-  bool dead = false;
-  int32_t attr = Rid;
-#pragma unroll
-  for (int j = 0; j < CM; j++) {
-    rd[j] = __ldcg(A.round + mem[j]);
-    if (rd[j] != 0u && rd[j] < t) dead = true;
-    else if (rd[j] == t && mem[j] < attr) attr = mem[j];
-  }
-  ls.listed++;
-  if (dead) {
-    if (EXACT && A.link_mode == 0) {
-      int32_t best = -1;
-      uint32_t bc = kNone;
-#pragma unroll
-      for (int j = 0; j < CM; j++) {
-        if (rd[j] != 0u && rd[j] < t) {
-          const uint32_t c = __ldcg(A.val + mem[j]);
-          if (c < bc) { bc = c; best = mem[j]; }
-        }
-      }
-      wl_add(W, A, Rid, best, ls);
-    }
-  } else if (attr == Rid) {
-#pragma unroll
-    for (int j = 0; j < CM; j++)
-      if (rd[j] == 0u || rd[j] > t) dec<EXACT>(A, mem[j], t, thr, nf, ls);
-    if (EXACT && A.link_mode == 0) {
-#pragma unroll
-      for (int j = 0; j < CM; j++)
-        if (rd[j] == t) wl_add(W, A, Rid, mem[j], ls);
-    }
-  }
-  if (EXACT && A.link_mode == 1) {
-#pragma unroll
-    for (int j = 0; j < CM; j++)
-      if (rd[j] != 0u && rd[j] <= t) wl_add(W, A, Rid, mem[j], ls);
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// re-listing of one frontier r-clique by one warp
-// ---------------------------------------------------------------------------------------------
-
-// Length of the list whose 32-entry chunks the re-listing of r-clique Rid walks: the adjacency
-// list of its vertex of least degree, or for (3,4) the shortest triangle list of its three edges.
-template <int R, int S>
-__device__ __forceinline__ int64_t relist_len(const GView& g, int32_t Rid) {
-  if constexpr (R == 1) {
-    return __ldg(g.off + Rid + 1) - __ldg(g.off + Rid);
-  } else if constexpr (R == 2) {
-    const int32_t u = __ldg(g.eu + Rid), v = __ldg(g.ev + Rid);
-    const int64_t du = __ldg(g.off + u + 1) - __ldg(g.off + u), dv = __ldg(g.off + v + 1) - __ldg(g.off + v);
-    return du < dv ? du : dv;
-  } else {
-    const int32_t v0 = __ldg(g.tri + 3 * (int64_t)Rid), v1 = __ldg(g.tri + 3 * (int64_t)Rid + 1),
-                  v2 = __ldg(g.tri + 3 * (int64_t)Rid + 2);
-    if constexpr (S == 4) {
-      const int64_t e[3] = {nh_edge_id(g, v0, v1), nh_edge_id(g, v0, v2), nh_edge_id(g, v1, v2)};
-      int64_t m = INT64_MAX;
-#pragma unroll
-      for (int i = 0; i < 3; i++) {
-        const int64_t len = e[i] < 0 ? 0 : __ldg(g.etoff + e[i] + 1) - __ldg(g.etoff + e[i]);
-        m = len < m ? len : m;
-      }
-      return m;
-    } else {
-      int64_t m = INT64_MAX;
-      const int32_t vv[3] = {v0, v1, v2};
-#pragma unroll
-      for (int i = 0; i < 3; i++) {
-        const int64_t len = __ldg(g.off + vv[i] + 1) - __ldg(g.off + vv[i]);
-        m = len < m ? len : m;
-      }
-      return m;
-    }
-  }
-}
-
-// chunks of 32 list entries per r-clique, the unit of work-proportional re-listing
-template <int R, int S>
-__global__ void k_chunk_cost(GView g, int64_t n_r, uint32_t* __restrict__ cost) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = (relist_len<R, S>(g, (int32_t)i) + 31) >> 5;
-    cost[i] = c > 0xffffffffll ? 0xffffffffu : (uint32_t)c;
-  }
-}
-
-// Re-lists the s-cliques of r-clique Rid found from chunks c0, c0 + cstep, ... (< cend) of its
-// list (chunk c = entries [32c, 32c + 32)).  For s - r = 2 the out-lists of the candidates found
-// in a chunk are split over Ge callers: this one expands candidates of lane index = se mod Ge.
-// The caller brackets the calls for one Rid with wl_begin / wl_flush (exact peel).
-template <int R, int S, bool EXACT>
-__device__ __noinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf, int lane,
-                            int64_t c0, int64_t cstep, int64_t cend, int Ge, int se, const WarpLinks& W,
-                            LocalStats& ls) {
-  constexpr int kPerLane = (S - R == 1) ? R : 5;  // link targets one lane can add per converged step
-  const GView& g = A.g;
-  int32_t vx[3] = {0, 0, 0};
-  int32_t eR[3] = {0, 0, 0};  // r = 3: edges (v0,v1), (v0,v2), (v1,v2)
-  if (R == 1) {
-    vx[0] = Rid;
-  } else if (R == 2) {
-    vx[0] = __ldg(g.eu + Rid);
-    vx[1] = __ldg(g.ev + Rid);
-  } else {
-    vx[0] = __ldg(g.tri + 3 * (int64_t)Rid);
-    vx[1] = __ldg(g.tri + 3 * (int64_t)Rid + 1);
-    vx[2] = __ldg(g.tri + 3 * (int64_t)Rid + 2);
-    int32_t mine = 0;
-    if (lane < 3) {
-      const int32_t x = (lane == 2) ? vx[1] : vx[0];
-      const int32_t y = (lane == 0) ? vx[1] : vx[2];
-      const int64_t p = nh_find(g.adj, __ldg(g.off + x), __ldg(g.off + x + 1), y);
-      mine = (p >= 0) ? __ldg(g.eid + p) : 0;
-    }
-    eR[0] = __shfl_sync(NH_FULL, mine, 0);
-    eR[1] = __shfl_sync(NH_FULL, mine, 1);
-    eR[2] = __shfl_sync(NH_FULL, mine, 2);
-  }
-  if constexpr (R == 3 && S == 4) {
-    // the 4-cliques on triangle R = {v0,v1,v2} are the w common to the triangle lists of its
-    // three edges; the ids of {v0,v1,w}, {v0,v2,w}, {v1,v2,w} are read from the list positions
-    int64_t tl[3], th[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-      tl[i] = __ldg(g.etoff + eR[i]);
-      th[i] = __ldg(g.etoff + eR[i] + 1);
-    }
-    int bt = 0;
-    if (th[1] - tl[1] < th[bt] - tl[bt]) bt = 1;
-    if (th[2] - tl[2] < th[bt] - tl[bt]) bt = 2;
-    if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(th[bt] - tl[bt]);
-    for (int64_t c = c0; c < cend && tl[bt] + 32 * c < th[bt]; c += cstep) {
-      const int64_t j = tl[bt] + 32 * c + lane;
-      bool ok = j < th[bt];
-      int32_t mem[3] = {0, 0, 0};
-      if (ok) {
-        const int32_t w = __ldg(g.etw + j);
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-          if (i == bt) {
-            mem[i] = __ldg(g.ettid + j);
-          } else if (ok) {
-            const int64_t p = nh_find(g.etw, tl[i], th[i], w);
-            if (p < 0) ok = false;
-            else mem[i] = __ldg(g.ettid + p);
-          }
-        }
-      }
-      if (ok) process_S<3, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-      if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
-    }
-    return;
-  }
-  int64_t lo[3], hi[3];
-#pragma unroll
-  for (int i = 0; i < R; i++) {
-    lo[i] = __ldg(g.off + vx[i]);
-    hi[i] = __ldg(g.off + vx[i] + 1);
-  }
-  int best = 0;
-#pragma unroll
-  for (int i = 1; i < R; i++)
-    if (hi[i] - lo[i] < hi[best] - lo[best]) best = i;
-  const int64_t b0 = lo[best], b1 = hi[best];
-  if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(b1 - b0);
-  for (int64_t c = c0; c < cend && b0 + 32 * c < b1; c += cstep) {
-    const int64_t j = b0 + 32 * c + lane;
-    bool ok = j < b1;
-    int32_t w = 0;
-    int32_t ew[3] = {0, 0, 0};
-    if (ok) {
-      w = __ldg(g.adj + j);
-#pragma unroll
-      for (int i = 0; i < R; i++) {
-        if (i == best) {
-          ew[i] = __ldg(g.eid + j);
-        } else if (ok) {
-          const int64_t id = nh_edge_id(g, vx[i], w);  // one probe instead of a binary search
-          if (id < 0) ok = false;
-          else ew[i] = (int32_t)id;
-        }
-      }
-    }
-    if constexpr (S - R == 1) {
-      if (ok) {
-        if constexpr (R == 1) {
-          const int32_t mem[1] = {w};
-          process_S<1, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-        } else if constexpr (R == 2) {
-          const int32_t mem[2] = {ew[0], ew[1]};
-          process_S<2, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-        } else {
-          const int32_t mem[3] = {
-              tri_id(A, nh_tri_key(vx[0], vx[1], w, eR[0], ew[0], ew[1]), ls),
-              tri_id(A, nh_tri_key(vx[0], vx[2], w, eR[1], ew[0], ew[2]), ls),
-              tri_id(A, nh_tri_key(vx[1], vx[2], w, eR[2], ew[1], ew[2]), ls)};
-          process_S<3, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-        }
-      }
-    } else {
-      // s - r = 2: pairs (w, x), x in N+(w) adjacent to every vertex of R, expanded across the
-      // warp so that lanes share the out-lists of the candidates found in this chunk
-      const uint32_t len =
-          (ok && (lane % Ge) == se) ? (uint32_t)(__ldg(g.ooff + w + 1) - __ldg(g.ooff + w)) : 0u;
-      uint32_t incl = len;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(NH_FULL, incl, d);
-        if (lane >= d) incl += o;
-      }
-      const uint32_t total = __shfl_sync(NH_FULL, incl, 31);
-      for (uint32_t pb = 0; pb < total; pb += 32) {
-        const uint32_t idx = pb + lane;
-        int own = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const uint32_t v = __shfl_sync(NH_FULL, incl, own + step - 1);
-          if (v <= idx) own += step;
-        }
-        const int32_t ow = __shfl_sync(NH_FULL, w, own);
-        const uint32_t oincl = __shfl_sync(NH_FULL, incl, own);
-        const uint32_t olen = __shfl_sync(NH_FULL, len, own);
-        const int32_t oe0 = __shfl_sync(NH_FULL, ew[0], own);
-        const int32_t oe1 = __shfl_sync(NH_FULL, ew[1], own);
-        if (idx < total) {
-          const int64_t q = __ldg(g.ooff + ow) + (int64_t)(idx - (oincl - olen));
-          const int32_t x = __ldg(g.oadj + q);
-          const int32_t e_wx = __ldg(g.oeid + q);
-          bool okx = true;
-          int32_t ex[2] = {0, 0};
-#pragma unroll
-          for (int i = 0; i < R; i++) {
-            if (!okx) break;
-            const int64_t id = nh_edge_id(g, vx[i], x);
-            if (id < 0) okx = false;
-            else ex[i] = (int32_t)id;
-          }
-          if (okx) {
-            if constexpr (R == 1) {
-              const int32_t mem[2] = {ow, x};
-              process_S<2, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-            } else if constexpr (R == 2) {
-              const int32_t mem[5] = {oe0, oe1, ex[0], ex[1], e_wx};
-              process_S<5, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
-            }
-          }
-        }
-        if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
-      }
-    }
-    if constexpr (EXACT && S - R == 1) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
-  }
-}
-
-// One r-clique re-listed by a group of G warps (this one is number sub): the warps take
-// interleaved chunks; for s - r = 2 they form G / Ge chunk-groups of Ge warps, the Ge warps of
-// one chunk-group scanning the same 32 candidates and each expanding the out-lists of every
-// Ge-th of them, so that the expansion of one heavy chunk is spread over Ge warps too.
-template <int R, int S, bool EXACT>
-__device__ __forceinline__ void relist_group(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, int32_t* nf,
-                                             int lane, int sub, int G, const WarpLinks& W, LocalStats& ls) {
-  const int Ge = (S - R == 2) ? (G < 32 ? G : 32) : 1;
-  const int Gc = G / Ge, sc = sub / Ge, se = sub % Ge;
-  if constexpr (EXACT) wl_begin(W, lane);
-  relist_item<R, S, EXACT>(A, Rid, t, thr, nf, lane, sc, Gc, INT64_MAX, Ge, se, W, ls);
-  if constexpr (EXACT) wl_flush(W, A, Rid, lane, ls);
-}
-
-// A list of at most kTaskItems r-cliques is cut into tasks of one 32-entry chunk each (for
-// s - r = 2: one Ge-th of a chunk's out-list expansions), which warps take from a shared counter,
-// so that a round lasts about its total work over the grid rather than its heaviest r-clique.
-// Every block builds the prefix sums of the chunk counts itself.  Block-collective; returns false
-// (having done nothing) when the chunk total does not fit 31 bits.
-template <int R, int S, bool EXACT>
-__device__ bool relist_tasks(const PeelArgs& A, const int32_t* items, unsigned int n, uint32_t t, uint32_t thr,
-                             int32_t* nf, int lane, long long nwarps, const WarpLinks& W, LocalStats& ls,
-                             uint32_t* s_pref, unsigned long long* s_wsum, unsigned long long* task_next) {
-  constexpr int kPer = kTaskItems / kThreads;
-  const unsigned int b = threadIdx.x * kPer;
-  uint32_t v[kPer];
-  unsigned long long sum = 0;
-#pragma unroll
-  for (int j = 0; j < kPer; j++) {
-    v[j] = (b + j < n) ? __ldg(A.cost + __ldcg(items + b + j)) : 0u;
-    sum += v[j];
-  }
-  unsigned long long incl = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned long long o = __shfl_up_sync(NH_FULL, incl, d);
-    if (lane >= d) incl += o;
-  }
-  __syncthreads();  // the previous call's readers of s_pref / s_wsum are done
-  if (lane == 31) s_wsum[threadIdx.x >> 5] = incl;
-  __syncthreads();
-  unsigned long long base = incl - sum, total = 0;
-  for (int w = 0; w < kThreads / 32; w++) {
-    const unsigned long long x = s_wsum[w];
-    if (w < (int)(threadIdx.x >> 5)) base += x;
-    total += x;
-  }
-  if (total >= (1ull << 31)) return false;
-#pragma unroll
-  for (int j = 0; j < kPer; j++) {
-    base += v[j];
-    if (b + j < n) s_pref[b + j] = (uint32_t)base;
-  }
-  __syncthreads();
-  int Ge = 1;
-  if constexpr (S - R == 2)
-    while (Ge < 32 && total * (unsigned long long)(2 * Ge) <= 4ull * (unsigned long long)nwarps) Ge *= 2;
-  const unsigned long long ntask = total * (unsigned long long)Ge;
-  const unsigned long long per = ntask / ((unsigned long long)nwarps * 8ull);
-  const unsigned long long bt = per > 0 ? per : 1ull;
-  int32_t curR = -1;
-  for (;;) {
-    unsigned long long k0 = 0;
-    if (lane == 0) k0 = atomicAdd(task_next, bt);
-    k0 = __shfl_sync(NH_FULL, k0, 0);
-    if (k0 >= ntask) break;
-    const unsigned long long k1 = k0 + bt < ntask ? k0 + bt : ntask;
-    for (unsigned long long k = k0; k < k1; k++) {
-      const uint32_t kc = (uint32_t)(k / (unsigned long long)Ge);
-      const int se = (int)(k % (unsigned long long)Ge);
-      unsigned int lo = 0, hi = n;  // first item whose inclusive prefix exceeds kc
-      while (lo < hi) {
-        const unsigned int mid = (lo + hi) >> 1;
-        if (s_pref[mid] <= kc) lo = mid + 1; else hi = mid;
-      }
-      const uint32_t cl = kc - (lo ? s_pref[lo - 1] : 0u);
-      const int32_t Rid = __ldcg(items + lo);
-      if (Rid != curR) {
-        if constexpr (EXACT) {
-          if (curR >= 0) wl_flush(W, A, curR, lane, ls);
-          wl_begin(W, lane);
-        }
-        curR = Rid;
-      }
-      relist_item<R, S, EXACT>(A, Rid, t, thr, nf, lane, cl, 1, (int64_t)cl + 1, Ge, se, W, ls);
-    }
-  }
-  if constexpr (EXACT) {
-    if (curR >= 0) wl_flush(W, A, curR, lane, ls);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------------------------
-// the persistent kernel
-// ---------------------------------------------------------------------------------------------
-
-template <bool EXACT>
-__device__ void leader_after_scan(const PeelArgs& A) {
-  PeelCtl* c = A.lk.ctl;
-  const unsigned int gm = c->gmin;
-  c->gmin = kNone;
-  c->alive_cur ^= 1u;
-  c->alive_n = c->alive2_count;
-  c->alive2_count = 0;
-  c->f_count = 0;
-  if (EXACT) {
-    if (gm != kNone && gm > c->thr) c->thr = gm;
-  } else {
-    while ((int)c->bucket + 1 < A.n_thr && A.thresholds[c->bucket] < gm) {
-      c->bucket++;
-      c->rounds_in_bucket = 0;
-    }
-    c->thr = A.thresholds[c->bucket];
-  }
-  c->st_levels++;
-}
-
-template <bool EXACT>
-__device__ void leader_end_of_round(const PeelArgs& A) {
-  PeelCtl* c = A.lk.ctl;
-  c->task_next = 0;
-  const unsigned int oc = c->ovf_cur;
-  if (c->ovf_count[oc] > 0) {
-    c->draining = 1;
-    c->drain_buf = oc;
-    c->drain_n = c->ovf_count[oc] < A.lk.ovf_cap ? c->ovf_count[oc] : A.lk.ovf_cap;
-    c->ovf_count[oc] = 0;
-    c->ovf_cur = oc ^ 1u;
-    return;
-  }
-  c->draining = 0;
-  c->finished += c->fsize;
-  c->st_rounds++;
-  c->st_front += c->fsize;
-  if (c->thr > c->kmax && c->fsize > 0) c->kmax = c->thr;
-  c->t++;
-  if (c->finished >= (unsigned long long)A.n_r) {
-    c->done = 1;
-    return;
-  }
-  if (!EXACT) {
-    if (++c->rounds_in_bucket >= A.T) {
-      if ((int)c->bucket + 1 < A.n_thr) c->bucket++;
-      c->rounds_in_bucket = 0;
-      c->thr = A.thresholds[c->bucket];
-      c->need_scan = 1;
-      c->nf_count = 0;
-      return;
-    }
-  }
-  if (c->nf_count > 0) {
-    c->cur ^= 1u;
-    c->fsize = c->nf_count;
-    c->nf_count = 0;
-    c->need_scan = 0;
-  } else {
-    c->need_scan = 1;
-  }
-}
-
-template <int R, int S, bool EXACT>
-__global__ void __launch_bounds__(kThreads) k_peel(PeelArgs A) {
-  PeelCtl* ctl = A.lk.ctl;
-  volatile PeelCtl* vc = ctl;
-  const int lane = threadIdx.x & 31;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
-  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
-  __shared__ int s_lcnt[kThreads / 32];
-  __shared__ int32_t s_seen[kThreads / 32][kSeen];
-  __shared__ uint32_t s_pref[kTaskItems];
-  __shared__ unsigned long long s_wsum[kThreads / 32];
-  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
-  __syncwarp();
-  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
-  for (;;) {
-    if (vc->done || vc->err) break;
-    if (vc->need_scan) {
-      // compact the live list and take the minimum count over it
-      {
-        const unsigned int ac = vc->alive_cur;
-        const int32_t* ain = A.alive[ac];
-        int32_t* aout = A.alive[ac ^ 1u];
-        const unsigned long long na = vc->alive_n;
-        const unsigned int t = vc->t;
-        uint32_t lmin = kNone;
-        for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
-             base += (unsigned long long)nwarps * 32) {
-          const unsigned long long i = base + lane;
-          bool live = false;
-          int32_t x = 0;
-          if (i < na) {
-            x = __ldcg(ain + i);
-            const uint32_t rd = __ldcg(A.round + x);
-            live = (rd == 0u || rd >= t);
-            if (live) lmin = min(lmin, __ldcg(A.cnt + x));
-          }
-          const unsigned long long pos = warp_append(&ctl->alive2_count, live, lane);
-          if (live) aout[pos] = x;
-        }
-        lmin = warp_min_u32(lmin);
-        if (lane == 0 && lmin != kNone) atomicMin(&ctl->gmin, lmin);
-      }
-      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_after_scan<EXACT>(A); })) break;
-      // frontier = live with count <= threshold
-      {
-        const int32_t* al = A.alive[vc->alive_cur];
-        const unsigned long long na = vc->alive_n;
-        const unsigned int thr = vc->thr, t = vc->t;
-        int32_t* fr = A.front[vc->cur];
-        for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
-             base += (unsigned long long)nwarps * 32) {
-          const unsigned long long i = base + lane;
-          bool take = false;
-          int32_t x = 0;
-          if (i < na) {
-            x = __ldcg(al + i);
-            take = __ldcg(A.cnt + x) <= thr;
-          }
-          const unsigned long long pos = warp_append(&ctl->f_count, take, lane);
-          if (take) {
-            fr[pos] = x;
-            __stcg(A.round + x, t);
-            __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
-          }
-        }
-      }
-      if (!grid_sync(ctl, A.timeout_ns, [&] {
-            ctl->fsize = ctl->f_count;
-            ctl->f_count = 0;
-          }))
-        break;
-    }
-    // re-list the frontier
-    {
-      const unsigned int t = vc->t, thr = vc->thr, cur = vc->cur;
-      const unsigned long long fs = vc->fsize;
-      const int32_t* fr = A.front[cur];
-      int32_t* nf = A.front[cur ^ 1u];
-      const bool tasks = fs <= (unsigned long long)kTaskItems &&
-                         relist_tasks<R, S, EXACT>(A, fr, (unsigned int)fs, t, thr, nf, lane, nwarps, W, ls, s_pref,
-                                                   s_wsum, &ctl->task_next);
-      if (!tasks) {
-        // a small frontier gets several warps per r-clique (G, a power of two up to 1024)
-        int G = 1;
-        while (G < A.gmax && (unsigned long long)(2 * G) * fs <= (unsigned long long)nwarps) G *= 2;
-        const long long ngroups = nwarps / G;
-        const long long grp = gwarp / G;
-        const int sub = (int)(gwarp % G);
-        if (grp < ngroups) {
-          for (unsigned long long it = (unsigned long long)grp; it < fs; it += (unsigned long long)ngroups)
-            relist_group<R, S, EXACT>(A, __ldcg(fr + it), t, thr, nf, lane, sub, G, W, ls);
-        }
-      }
-    }
-    // end of round: drain deferred link calls, then advance
-    bool ok = true;
-    for (;;) {
-      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_end_of_round<EXACT>(A); })) { ok = false; break; }
-      if (!vc->draining) break;
-      const int2* q = A.lk.ovf[vc->drain_buf];
-      const unsigned long long nq = vc->drain_n;
-      for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-           i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int2 p = __ldcg(q + i);
-        link_run(A.lk, p.x, p.y, ls);
-      }
-    }
-    if (!ok) break;
-  }
-  if (A.stats) {
-    const unsigned long long v0 = warp_sum_u64(ls.listed), v1 = warp_sum_u64(ls.dec), v2 = warp_sum_u64(ls.link),
-                             v3 = warp_sum_u64(ls.unite), v4 = warp_sum_u64(ls.scan), v5 = warp_sum_u64(ls.probe),
-                             v6 = warp_sum_u64(ls.ovf);
-    if (lane == 0) {
-      atomicAdd(&ctl->st_listed, v0);
-      atomicAdd(&ctl->st_dec, v1);
-      atomicAdd(&ctl->st_link, v2);
-      atomicAdd(&ctl->st_unite, v3);
-      atomicAdd(&ctl->st_scan, v4);
-      atomicAdd(&ctl->st_probe, v5);
-      atomicAdd(&ctl->st_ovf, v6);
-    }
-  }
-}
+namespace nhp {
 
 __global__ void k_peel_init(int64_t n_r, const uint32_t* __restrict__ cnt0, uint32_t* __restrict__ cnt,
                             uint32_t* __restrict__ round, uint32_t* __restrict__ val, int32_t* __restrict__ alive,
@@ -1077,41 +89,30 @@ __global__ void k_link_drain(LinkEnv E) {
   }
 }
 
-template <int R, int S, bool EXACT>
-int launch_peel(PeelArgs& A, cudaStream_t st) {
-  const void* fn = (const void*)k_peel<R, S, EXACT>;
-  int dev = 0, sms = 0, per = 0, coop = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return NH_ERR_UNSUPPORTED;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1)
-    return NH_ERR_CUDA;
-  dim3 grid((unsigned)(sms * per)), block(kThreads);
-  void* args[] = {&A};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st);
-  nh_note_launch();
-  return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
-}
-
-template <bool EXACT>
-int dispatch(int r, int s, PeelArgs& A, cudaStream_t st) {
-  if (r == 1 && s == 2) return launch_peel<1, 2, EXACT>(A, st);
-  if (r == 1 && s == 3) return launch_peel<1, 3, EXACT>(A, st);
-  if (r == 2 && s == 3) return launch_peel<2, 3, EXACT>(A, st);
-  if (r == 2 && s == 4) return launch_peel<2, 4, EXACT>(A, st);
-  if (r == 3 && s == 4) return launch_peel<3, 4, EXACT>(A, st);
+int peel_launch_pair(int r, int s, bool exact, PeelArgs& A, cudaStream_t st) {
+  if (r == 1 && s == 2) return peel_launch_12(exact, A, st);
+  if (r == 1 && s == 3) return peel_launch_13(exact, A, st);
+  if (r == 2 && s == 3) return peel_launch_23(exact, A, st);
+  if (r == 2 && s == 4) return peel_launch_24(exact, A, st);
+  if (r == 3 && s == 4) return peel_launch_34(exact, A, st);
   return NH_ERR_UNSUPPORTED;
 }
 
-int launch_chunk_cost(int r, int s, const GView& g, int64_t n_r, uint32_t* cost, cudaStream_t st) {
-  const unsigned blocks = nh_blocks_for(n_r, 256, 152 * 16);
-  if (r == 1) k_chunk_cost<1, 2><<<blocks, 256, 0, st>>>(g, n_r, cost);
-  else if (r == 2) k_chunk_cost<2, 3><<<blocks, 256, 0, st>>>(g, n_r, cost);
-  else if (r == 3 && s == 4) k_chunk_cost<3, 4><<<blocks, 256, 0, st>>>(g, n_r, cost);
-  else return NH_ERR_UNSUPPORTED;
-  nh_note_launch();
-  return NH_OK;
+int two_phase_launch_pair(int r, int s, PeelArgs& A, TreeOut& T, cudaStream_t st) {
+  if (r == 1 && s == 2) return two_phase_launch_12(A, T, st);
+  if (r == 1 && s == 3) return two_phase_launch_13(A, T, st);
+  if (r == 2 && s == 3) return two_phase_launch_23(A, T, st);
+  if (r == 2 && s == 4) return two_phase_launch_24(A, T, st);
+  if (r == 3 && s == 4) return two_phase_launch_34(A, T, st);
+  return NH_ERR_UNSUPPORTED;
+}
+
+// chunk counts of the re-listed lists (they depend on r, and for r = 3 on s)
+int chunk_cost_pair(int r, int s, const GView& g, int64_t n_r, uint32_t* cost, cudaStream_t st) {
+  if (r == 1) return chunk_cost_12(g, n_r, cost, st);
+  if (r == 2) return chunk_cost_23(g, n_r, cost, st);
+  if (r == 3 && s == 4) return chunk_cost_34(g, n_r, cost, st);
+  return NH_ERR_UNSUPPORTED;
 }
 
 // shared driver for the exact and the approximate peel
@@ -1139,6 +140,10 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   A.link_mode = exact ? link_mode : -1;
   A.stats = stats != nullptr;
   A.gmax = g_peel_max_group;
+  // automatic: link-efficient chains the targets of one r-clique per warp, so spreading its chunks
+  // over many warps repeats walks; for s - r = 1 that costs more than the balance gains
+  A.task_items = (unsigned int)(g_peel_task_items >= 0 ? g_peel_task_items
+                                : (exact && link_mode < 2 && s - r == 1) ? 0 : kTaskItems);
   A.timeout_ns = 60ull * 1000000000ull;
   A.lk.uf = uf;
   A.lk.L = L;
@@ -1155,7 +160,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
       (rc = nh_alloc(&cost, n_r, st))) {
     goto cleanup;
   }
-  if ((rc = launch_chunk_cost(r, s, A.g, n_r, cost, st))) goto cleanup;
+  if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
   if (exact) {
     if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
@@ -1201,7 +206,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
                                                                   exact ? uf : nullptr, exact ? L : nullptr);
   nh_note_launch();
   if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
-  rc = exact ? dispatch<true>(r, s, A, st) : dispatch<false>(r, s, A, st);
+  rc = peel_launch_pair(r, s, exact, A, st);
   if (!rc) {
     PeelCtl h{};
     cudaMemcpyAsync(&h, A.lk.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
@@ -1231,7 +236,9 @@ cleanup:
   return rc;
 }
 
-}  // namespace
+}  // namespace nhp
+
+using namespace nhp;
 
 extern "C" int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* core,
                                 uint32_t* round, int32_t* uf, int32_t* L, int link_mode, nh_peel_stats* stats,
@@ -1289,102 +296,7 @@ extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int
 // per level.
 // ---------------------------------------------------------------------------------------------
 
-namespace {
-
-struct TreeOut {
-  const int32_t* order;    // r-cliques sorted by core (any order within a level)
-  const int64_t* lvl_off;  // [kmax + 2]
-  uint32_t kmax;
-  uint32_t* lvl;           // per root: last level it got a node
-  int32_t* nid;            // per root: that node
-  int32_t* top;            // per root: current top node of its component
-  int32_t* parent;         // [n_r + nodes]
-  uint32_t* label;
-  unsigned long long* node_count;
-};
-
-template <int R, int S>
-__global__ void __launch_bounds__(kThreads) k_two_phase(PeelArgs A, TreeOut T) {
-  PeelCtl* ctl = A.lk.ctl;
-  volatile PeelCtl* vc = ctl;
-  const int lane = threadIdx.x & 31;
-  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
-  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
-  __shared__ int s_lcnt[kThreads / 32];
-  __shared__ int32_t s_seen[kThreads / 32][kSeen];
-  __shared__ uint32_t s_pref[kTaskItems];
-  __shared__ unsigned long long s_wsum[kThreads / 32];
-  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
-  __syncwarp();
-  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
-  const int64_t n_r = A.n_r;
-  for (uint32_t level = T.kmax; level >= 1; --level) {
-    const int64_t lo = T.lvl_off[level], hi = T.lvl_off[level + 1];
-    const unsigned long long cnt = (unsigned long long)(hi - lo);
-    if (cnt == 0) continue;
-    // unions at this level
-    const bool tasks = cnt <= (unsigned long long)kTaskItems &&
-                       relist_tasks<R, S, true>(A, T.order + lo, (unsigned int)cnt, 0u, level, nullptr, lane,
-                                                nwarps, W, ls, s_pref, s_wsum, &ctl->task_next);
-    if (!tasks) {
-      int G = 1;
-      while (G < A.gmax && (unsigned long long)(2 * G) * cnt <= (unsigned long long)nwarps) G *= 2;
-      const long long ngroups = nwarps / G, grp = gwarp / G;
-      const int sub = (int)(gwarp % G);
-      if (grp < ngroups)
-        for (unsigned long long it = (unsigned long long)grp; it < cnt; it += (unsigned long long)ngroups)
-          relist_group<R, S, true>(A, T.order[lo + it], 0u, level, nullptr, lane, sub, G, W, ls);
-    }
-    if (!grid_sync(ctl, A.timeout_ns, [&] { ctl->task_next = 0; })) break;
-    // a node for every component holding an r-clique of this level
-    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
-      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
-      uint32_t cur = __ldcg(T.lvl + y);
-      while (cur != level) {
-        const uint32_t prev = atomicCAS(T.lvl + y, cur, level);
-        if (prev == cur) {
-          const int32_t id = (int32_t)atomicAdd(T.node_count, 1ull);
-          T.nid[y] = id;
-          T.label[id] = level;
-          T.parent[n_r + id] = -1;
-          break;
-        }
-        cur = prev;
-      }
-    }
-    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
-    // leaves of this level, and previous top nodes of every joined component
-    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
-      const int32_t R0 = T.order[lo + i];
-      T.parent[R0] = __ldcg(T.nid + uf_find(A.lk.uf, R0));
-    }
-    {
-      const unsigned long long nt = *(volatile unsigned long long*)A.touched_n;
-      for (unsigned long long i = (unsigned long long)gtid; i < nt; i += (unsigned long long)nthreads) {
-        const int32_t x = __ldcg(A.touched + i);
-        const int32_t tp = __ldcg(T.top + x);
-        if (tp >= 0) T.parent[n_r + tp] = __ldcg(T.nid + uf_find(A.lk.uf, x));
-      }
-    }
-    if (!grid_sync(ctl, A.timeout_ns, [&] { *A.touched_n = 0; })) break;
-    for (long long i = gtid; i < (long long)cnt; i += nthreads) {
-      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
-      T.top[y] = __ldcg(T.nid + y);
-    }
-    if (!grid_sync(ctl, A.timeout_ns, [] {})) break;
-  }
-  if (A.stats) {
-    const unsigned long long v0 = warp_sum_u64(ls.listed), v3 = warp_sum_u64(ls.unite);
-    if (lane == 0) {
-      atomicAdd(&ctl->st_listed, v0);
-      atomicAdd(&ctl->st_unite, v3);
-    }
-  }
-}
+namespace nhp {
 
 __global__ void k_core_hist(int64_t n_r, const uint32_t* __restrict__ core, uint32_t* __restrict__ hist) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x)
@@ -1409,20 +321,7 @@ __global__ void k_two_phase_init(int64_t n_r, int32_t* __restrict__ uf, uint32_t
   }
 }
 
-template <int R, int S>
-int launch_two_phase(PeelArgs& A, TreeOut& T, cudaStream_t st) {
-  const void* fn = (const void*)k_two_phase<R, S>;
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1) return NH_ERR_CUDA;
-  void* args[] = {&A, &T};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(sms * per)), dim3(kThreads), args, 0, st);
-  nh_note_launch();
-  return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
-}
-
-}  // namespace
+}  // namespace nhp
 
 extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
                                       int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
@@ -1443,6 +342,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   A.val = const_cast<uint32_t*>(core);
   A.union_mode = 1;
   A.gmax = g_peel_max_group;
+  A.task_items = (unsigned int)(g_peel_task_items >= 0 ? g_peel_task_items : kTaskItems);
   A.link_mode = -1;
   A.stats = 0;
   A.timeout_ns = 60ull * 1000000000ull;
@@ -1460,7 +360,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
       (rc = nh_alloc(&T.top, n_r, st)) || (rc = nh_alloc(&T.node_count, 1, st)) || (rc = nh_alloc(&dmax, 1, st)) ||
       (rc = nh_alloc(&order, n_r, st)) || (rc = nh_alloc(&cost, n_r, st)))
     goto cleanup;
-  if ((rc = launch_chunk_cost(r, s, A.g, n_r, cost, st))) goto cleanup;
+  if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
   cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
   k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, core, dmax);
@@ -1487,11 +387,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   T.parent = parent;
   T.label = label;
   if (kmax >= 1) {
-    if (r == 1 && s == 2) rc = launch_two_phase<1, 2>(A, T, st);
-    else if (r == 1 && s == 3) rc = launch_two_phase<1, 3>(A, T, st);
-    else if (r == 2 && s == 3) rc = launch_two_phase<2, 3>(A, T, st);
-    else if (r == 2 && s == 4) rc = launch_two_phase<2, 4>(A, T, st);
-    else rc = launch_two_phase<3, 4>(A, T, st);
+    rc = two_phase_launch_pair(r, s, A, T, st);
   }
   if (!rc) {
     PeelCtl h{};
@@ -1513,5 +409,11 @@ cleanup:
 extern "C" int nh_set_peel_max_group(int g) {
   if (g < 1 || g > 1024 || (g & (g - 1))) return NH_ERR_INVALID;
   g_peel_max_group = g;
+  return NH_OK;
+}
+
+extern "C" int nh_set_peel_task_items(int n) {
+  if (n < -1 || n > kTaskItems) return NH_ERR_INVALID;
+  g_peel_task_items = n;
   return NH_OK;
 }

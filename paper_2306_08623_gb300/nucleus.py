@@ -62,6 +62,7 @@ def lib():
             "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_hierarchy_two_phase": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
             "nh_set_peel_max_group": (I32, [I32]),
+            "nh_set_peel_task_items": (I32, [I32]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
@@ -342,6 +343,12 @@ def set_peel_max_group(g: int):
     """Largest number of warps per frontier r-clique (power of two, 1..1024); results never
     depend on it."""
     _check("nh_set_peel_max_group", lib().nh_set_peel_max_group(int(g)))
+
+
+def set_peel_task_items(n: int):
+    """Largest frontier (or level) re-listed as work-proportional chunk tasks (0..4096, 0 = off,
+    -1 = automatic); results never depend on it."""
+    _check("nh_set_peel_task_items", lib().nh_set_peel_task_items(int(n)))
 
 
 def autotune_peel_max_group(run, candidates=(16, 64, 256, 1024), repeats: int = 1) -> dict:

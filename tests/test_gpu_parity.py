@@ -309,3 +309,33 @@ def test_hierarchy_methods(nc, r, s, method):
         assert np.array_equal(u32(pk["core"]), ref["core"])
         # the peel is round-synchronous, so its round stamps do not depend on linking
         assert np.array_equal(u32(pk["round"]), u32(res["round"]))
+
+
+@pytest.mark.parametrize("r,s", SUPPORTED)
+def test_tuning_knobs_do_not_change_results(nc, r, s):
+    """Work-proportional tasks on or off, and any warp-group cap, give the oracle's cores, round
+    stamps and hierarchy (both hierarchy methods; the approximate peel too)."""
+    off, adj = gg.rmat(12, 16, 7)
+    ref = oracle.nucleus(off, adj, r, s)
+    ra = oracle.nucleus(off, adj, r, s, hier=None, approx_delta=0.5)
+    d_off, d_adj = to_dev(off, adj)
+    rounds = None
+    try:
+        for items, gmax in [(0, 1024), (0, 1), (4096, 1024), (64, 4), (1, 32), (-1, 1024)]:
+            nc.set_peel_task_items(items)
+            nc.set_peel_max_group(gmax)
+            for method in ("el", "te"):
+                res = nc.hierarchy(d_off, d_adj, r, s, method=method)
+                assert np.array_equal(u32(res["core"]), ref["core"]), (items, gmax, method)
+                compare_hierarchy(res["parent"].cpu().numpy(), u32(res["label"]), res["n_nodes"], ref["leaf_node"],
+                                  ref["node_parent"], ref["node_label"])
+                if rounds is None:
+                    rounds = u32(res["round"])
+                assert np.array_equal(u32(res["round"]), rounds)
+            a = nc.approx_nucleus(res["oriented"], res["rindex"], s, 0.5, res["cnt"])
+            assert np.array_equal(u32(a["approx"]), ra["approx"])
+        with pytest.raises(nc.NucleusError):
+            nc.set_peel_task_items(4097)
+    finally:
+        nc.set_peel_task_items(-1)
+        nc.set_peel_max_group(1024)
