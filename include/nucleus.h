@@ -211,6 +211,21 @@ int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t* off_out, 
 /* rbase int64[n_graphs+1] (host): first r-clique id of each graph of a union built from vbase */
 int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream);
 
+/* The whole exact path for one (r,s) on an existing r-clique index -- s-clique counts (as
+ * nh_count_s_cliques), the peel with link-efficient in link mode 0 (as nh_peel_and_link) and
+ * construct-tree (as nh_construct_tree) -- in stream order with no host synchronisation and no
+ * read-back, so that a caller can capture the sequence into a CUDA graph (stream capture) and
+ * replay it.  Working memory is taken and returned with cudaMallocAsync / cudaFreeAsync on the
+ * stream.  Outputs (device, caller-owned): cnt, core, round, uf, L [n_r]; parent [2 n_r];
+ * label [n_r]; res (int64 [4]) = {status, n_s, n_nodes, rounds}, valid once the stream reaches
+ * the end of the sequence; status is 0 or the first NH_ERR_* a step recorded (a step after a
+ * failed one still runs, on whatever its inputs hold, and cannot change a recorded status).
+ * Return value: argument / launch errors found while enqueuing (NH_ERR_INVALID, NH_ERR_OOM,
+ * NH_ERR_UNSUPPORTED, NH_ERR_CUDA). */
+int nh_hierarchy_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint32_t* core,
+                         uint32_t* round, int32_t* uf, int32_t* L, int32_t* parent, uint32_t* label,
+                         int64_t* res, void* stream);
+
 /* Tuning knob of the peel and two-phase kernels (process-wide, default 1024): the largest number
  * of warps that share one frontier r-clique when the frontier is small.  More warps shorten a
  * round's critical path; with link-efficient each warp chains its own link targets, so more

@@ -202,10 +202,14 @@ int grid_for(const void* fn, int threads, size_t smem) {
   return sms * per;
 }
 
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
 }  // namespace
 
-int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
-                  const float* vertex_cost, float* measure, cudaStream_t st) {
+// Stream-ordered counting: launches only (no host synchronisation), the s-clique total into
+// dcount and an error code into status (both device words the caller provides and zeroes).
+int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, const float* vertex_cost,
+                     float* measure, unsigned long long* dcount, int* status, cudaStream_t st) {
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
   if (!nh_supported(r, s) && !(r == 1 && s == 4)) return NH_ERR_UNSUPPORTED;
@@ -214,34 +218,20 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
   if (r == 1 && s == 2) {
     k_count_12<<<nh_blocks_for(o->n, 256, 152 * 32), 256, 0, st>>>(o->n, o->off, cnt);
     nh_note_launch();
-    if (cudaGetLastError() != cudaSuccess) return NH_ERR_CUDA;
-    if (n_s) {
-      if (cudaStreamSynchronize(st) != cudaSuccess) return NH_ERR_CUDA;
-      *n_s = (uint64_t)o->m;
-    }
-    return NH_OK;
+    k_set_u64<<<1, 1, 0, st>>>(dcount, (unsigned long long)o->m);
+    nh_note_launch();
+    return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
   }
-  unsigned long long* dcount = nullptr;
-  int* status = nullptr;
   int32_t* scratch = nullptr;
   int32_t* order = nullptr;
   unsigned long long* next = nullptr;
   int rc = NH_OK;
-  if ((rc = nh_alloc(&dcount, 1, st)) || (rc = nh_alloc(&status, 1, st))) {
-    nh_free(dcount, st); nh_free(status, st);
-    return rc;
-  }
   if (measure) cudaMemsetAsync(measure, 0, sizeof(float) * (size_t)o->n, st);
-  cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(status, 0, sizeof(int), st);
   cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ri->n_r, st);
   if (s == 3) {
     const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
     int grid = grid_for(fn, kThreads, 0);
-    if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) {
-      nh_free(dcount, st); nh_free(status, st);
-      return rc;
-    }
+    if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) return rc;
     if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
     else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
     nh_note_launch();
@@ -252,13 +242,10 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
     const void* fn = (r == 1) ? (const void*)k_count_s4<1> : (r == 2) ? (const void*)k_count_s4<2> : (const void*)k_count_s4<3>;
     if (use_smem) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int grid = grid_for(fn, kThreads, use_smem ? smem : 0);
-    if (!use_smem && (rc = nh_alloc(&scratch, (int64_t)grid * kWarpsPerBlock * 3 * cap, st))) {
-      nh_free(dcount, st); nh_free(status, st);
-      return rc;
-    }
+    if (!use_smem && (rc = nh_alloc(&scratch, (int64_t)grid * kWarpsPerBlock * 3 * cap, st))) return rc;
     const size_t dyn = use_smem ? smem : 0;
     if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) {
-      nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st);
+      nh_free(scratch, st);
       return rc;
     }
     if (r == 1) k_count_s4<1><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
@@ -267,11 +254,29 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
     nh_note_launch();
   }
   if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+  nh_free(scratch, st); nh_free(order, st); nh_free(next, st);
+  return rc;
+}
+
+int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint64_t* n_s,
+                  const float* vertex_cost, float* measure, cudaStream_t st) {
+  unsigned long long* dcount = nullptr;
+  int* status = nullptr;
+  int rc = NH_OK;
+  if ((rc = nh_alloc(&dcount, 1, st)) || (rc = nh_alloc(&status, 1, st))) {
+    nh_free(dcount, st); nh_free(status, st);
+    return rc;
+  }
+  cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  rc = nh_count_enqueue(o, ri, s, cnt, vertex_cost, measure, dcount, status, st);
   unsigned long long hcount = 0;
   int hs = 0;
-  cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  nh_free(dcount, st); nh_free(status, st); nh_free(scratch, st); nh_free(order, st); nh_free(next, st);
+  if (!rc) {
+    cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  }
+  nh_free(dcount, st); nh_free(status, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (!rc && hs) rc = hs;
   if (!rc && n_s) *n_s = hcount;

@@ -9,7 +9,9 @@
 //   eu[m], ev[m]    endpoints of edge id e (eu < ev)
 //   tri[3 n_r]      vertices of triangle id t (r = 3), toff[m+1] (i64) first triangle id per edge
 //   table[cap]      16-byte slots {key u64, id u32, pad}: key = (edge id of (a,b)) << 32 | c
-//   ehash[cap]      16-byte slots keyed by (u << 32 | v), u < v, holding the edge id (load <= 0.5)
+//   ekey[cap] (u64), eval[cap]   open-addressing edge table (load <= 0.5): key (u << 32 | v), u < v,
+//                   and the edge id in the parallel value array (a miss reads the 8-byte keys only,
+//                   so the key array of a few-million-edge graph stays resident in L2)
 //   etoff[m+1] (i64), etw[3 n_r], ettid[3 n_r]   r = 3: for every edge (p,q), the third vertices w
 //                   of all triangles {p,q,w} in ascending order, with the triangle ids
 #pragma once
@@ -41,7 +43,8 @@ struct nh_oriented {
   int32_t* eu;
   int32_t* ev;
   int64_t max_out, max_deg;
-  nh_slot* ehash;
+  unsigned long long* ekey;
+  uint32_t* eval;
   unsigned long long emask;
   cudaStream_t stream;  // stream the handle was built on (frees are ordered on it)
 };
@@ -71,7 +74,8 @@ struct GView {
   const int32_t* osrc;
   const int32_t* eu;
   const int32_t* ev;
-  const nh_slot* ehash;
+  const unsigned long long* ekey;
+  const uint32_t* eval;
   unsigned long long emask;
   const int32_t* tri;
   const nh_slot* table;
@@ -87,7 +91,7 @@ static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
   g.off = o->off; g.adj = o->adj; g.eid = o->eid;
   g.ooff = o->ooff; g.oadj = o->oadj; g.oeid = o->oeid; g.osrc = o->osrc;
   g.eu = o->eu; g.ev = o->ev;
-  g.ehash = o->ehash; g.emask = o->emask;
+  g.ekey = o->ekey; g.eval = o->eval; g.emask = o->emask;
   g.tri = ri ? ri->tri : nullptr;
   g.table = ri ? ri->table : nullptr;
   g.mask = ri ? ri->mask : 0ull;
@@ -154,7 +158,14 @@ __device__ __forceinline__ int64_t nh_tri_lookup(const nh_slot* __restrict__ t, 
 __device__ __forceinline__ int64_t nh_edge_id(const GView& g, int32_t x, int32_t y) {
   const unsigned long long key = (x < y) ? (((unsigned long long)(uint32_t)x << 32) | (uint32_t)y)
                                          : (((unsigned long long)(uint32_t)y << 32) | (uint32_t)x);
-  return nh_tri_lookup(g.ehash, g.emask, key);
+  unsigned long long h = nh_mix64(key) & g.emask;
+  for (unsigned long long p = 0; p <= g.emask; ++p) {
+    const unsigned long long k = __ldg(g.ekey + h);
+    if (k == key) return (int64_t)__ldg(g.eval + h);
+    if (k == NH_EMPTY_KEY) return -1;
+    h = (h + 1) & g.emask;
+  }
+  return -1;
 }
 
 __device__ __forceinline__ unsigned long long nh_globaltimer() {
@@ -201,6 +212,12 @@ int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream
 // block sums a scan of n entries needs, and the scan with caller-provided block-sum storage
 int nh_scan_u32_blocks(int64_t n);
 int nh_exclusive_scan_u32_into(const uint32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t st);
+
+// stream-ordered pieces of the path (no host synchronisation; results stay in device words)
+int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, const float* vertex_cost,
+                     float* measure, unsigned long long* dcount, int* status, cudaStream_t st);
+int nh_tree_enqueue(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
+                    uint32_t* label, int64_t* n_nodes_dev, cudaStream_t st);
 
 // allocation helpers (stream ordered)
 template <typename T>

@@ -242,15 +242,16 @@ __global__ void k_et_fill(int64_t m, const int64_t* __restrict__ off, const int3
 }
 
 __global__ void k_edge_insert(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                              nh_slot* __restrict__ table, unsigned long long mask, int* __restrict__ status) {
+                              unsigned long long* __restrict__ ekey, uint32_t* __restrict__ eval,
+                              unsigned long long mask, int* __restrict__ status) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long key = ((unsigned long long)(uint32_t)eu[e] << 32) | (uint32_t)ev[e];
     unsigned long long h = nh_mix64(key) & mask;
     bool done = false;
     for (unsigned long long p = 0; p <= mask; ++p) {
-      const unsigned long long old = atomicCAS(&table[h].key, NH_EMPTY_KEY, key);
+      const unsigned long long old = atomicCAS(ekey + h, NH_EMPTY_KEY, key);
       if (old == NH_EMPTY_KEY || old == key) {
-        table[h].val = (uint32_t)e;
+        eval[h] = (uint32_t)e;
         done = true;
         break;
       }
@@ -258,6 +259,12 @@ __global__ void k_edge_insert(int64_t m, const int32_t* __restrict__ eu, const i
     }
     if (!done) atomicExch(status, NH_ERR_TABLE_FULL);
   }
+}
+
+__global__ void k_fill_empty_keys(unsigned long long* k, unsigned long long cap) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    k[i] = NH_EMPTY_KEY;
 }
 
 __global__ void k_fill_empty(nh_slot* t, unsigned long long cap) {
@@ -288,7 +295,7 @@ unsigned warp_grid(int64_t items) {
 void free_oriented(nh_oriented* o) {
   if (!o) return;
   cudaFree(o->eid); cudaFree(o->ooff); cudaFree(o->oadj); cudaFree(o->oeid); cudaFree(o->osrc);
-  cudaFree(o->uoff); cudaFree(o->eu); cudaFree(o->ev); cudaFree(o->ehash);
+  cudaFree(o->uoff); cudaFree(o->eu); cudaFree(o->ev); cudaFree(o->ekey); cudaFree(o->eval);
   delete o;
 }
 
@@ -376,7 +383,8 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
     unsigned long long cap = 1024;
     while (cap < 2ull * (unsigned long long)m) cap <<= 1;
     int* status = nullptr;
-    if ((rc = nh_alloc(&o->ehash, (int64_t)cap, st)) || (rc = nh_alloc(&status, 1, st))) {
+    if ((rc = nh_alloc(&o->ekey, (int64_t)cap, st)) || (rc = nh_alloc(&o->eval, (int64_t)cap, st)) ||
+        (rc = nh_alloc(&status, 1, st))) {
       nh_free(status, st);
       cudaStreamSynchronize(st);
       free_oriented(o);
@@ -384,9 +392,10 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
     }
     o->emask = cap - 1;
     cudaMemsetAsync(status, 0, sizeof(int), st);
-    k_fill_empty<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(o->ehash, cap);
+    k_fill_empty_keys<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(o->ekey, cap);
     nh_note_launch();
-    k_edge_insert<<<nh_blocks_for(m, 256, 152 * 32), 256, 0, st>>>(m, o->eu, o->ev, o->ehash, o->emask, status);
+    k_edge_insert<<<nh_blocks_for(m, 256, 152 * 32), 256, 0, st>>>(m, o->eu, o->ev, o->ekey, o->eval, o->emask,
+                                                                    status);
     nh_note_launch();
     int hs = 0;
     cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -43,6 +43,15 @@ __global__ void k_peel_init(int64_t n_r, const uint32_t* __restrict__ cnt0, uint
   }
 }
 
+__global__ void k_peel_result(const PeelCtl* c, int64_t* res) {
+  if (res[0] == 0) res[0] = c->err ? c->err : (c->done ? NH_OK : NH_ERR_INTERNAL);
+  res[3] = (int64_t)c->st_rounds;
+}
+
+__global__ void k_status_into(const int* status, int64_t* res) {
+  if (res[0] == 0 && *status) res[0] = *status;
+}
+
 __global__ void k_ctl_init(PeelCtl* c, int64_t n_r, unsigned int thr0) {
   c->t = 1;
   c->thr = thr0;
@@ -116,9 +125,13 @@ int chunk_cost_pair(int r, int s, const GView& g, int64_t n_r, uint32_t* cost, c
 }
 
 // shared driver for the exact and the approximate peel
+// res_dev == nullptr: synchronous (status returned, stats read back).  Otherwise exact only and
+// stream ordered: nothing is read back; the status goes to res_dev[0] (unless it already holds
+// one) and the round count to res_dev[3].
 int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* val,
              uint32_t* round, int32_t* uf, int32_t* L, int link_mode, double delta, nh_peel_stats* stats,
-             cudaStream_t st) {
+             int64_t* res_dev, cudaStream_t st) {
+  if (res_dev && !exact) return NH_ERR_INVALID;
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
   if (stats) *stats = nh_peel_stats{};
@@ -207,7 +220,10 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   nh_note_launch();
   if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
   rc = peel_launch_pair(r, s, exact, A, st);
-  if (!rc) {
+  if (!rc && res_dev) {
+    k_peel_result<<<1, 1, 0, st>>>(A.lk.ctl, res_dev);
+    nh_note_launch();
+  } else if (!rc) {
     PeelCtl h{};
     cudaMemcpyAsync(&h, A.lk.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
@@ -232,6 +248,7 @@ cleanup:
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
   nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
   nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st);
+  if (res_dev) return (cudaGetLastError() != cudaSuccess && !rc) ? NH_ERR_CUDA : rc;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }
@@ -243,12 +260,38 @@ using namespace nhp;
 extern "C" int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* core,
                                 uint32_t* round, int32_t* uf, int32_t* L, int link_mode, nh_peel_stats* stats,
                                 void* stream) {
-  return run_peel(true, o, ri, s, cnt, core, round, uf, L, link_mode, 0.0, stats, (cudaStream_t)stream);
+  return run_peel(true, o, ri, s, cnt, core, round, uf, L, link_mode, 0.0, stats, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double delta, const uint32_t* cnt,
                                  uint32_t* approx, uint32_t* round, nh_peel_stats* stats, void* stream) {
-  return run_peel(false, o, ri, s, cnt, approx, round, nullptr, nullptr, -1, delta, stats, (cudaStream_t)stream);
+  return run_peel(false, o, ri, s, cnt, approx, round, nullptr, nullptr, -1, delta, stats, nullptr,
+                  (cudaStream_t)stream);
+}
+
+extern "C" int nh_hierarchy_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, uint32_t* core,
+                                    uint32_t* round, int32_t* uf, int32_t* L, int32_t* parent, uint32_t* label,
+                                    int64_t* res, void* stream) {
+  if (!o || !ri || ri->o != o || !res) return NH_ERR_INVALID;
+  if (!nh_supported(ri->r, s)) return NH_ERR_UNSUPPORTED;
+  const int64_t n_r = ri->n_r;
+  if (n_r > 0 && (!cnt || !core || !round || !uf || !L || !parent || !label)) return NH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(res, 0, 4 * sizeof(int64_t), st) != cudaSuccess) return NH_ERR_CUDA;
+  if (n_r == 0) return NH_OK;
+  int* cstat = nullptr;
+  int rc = nh_alloc(&cstat, 1, st);
+  if (rc) return rc;
+  cudaMemsetAsync(cstat, 0, sizeof(int), st);
+  rc = nh_count_enqueue(o, ri, s, cnt, nullptr, nullptr, reinterpret_cast<unsigned long long*>(res + 1), cstat, st);
+  if (!rc) {
+    k_status_into<<<1, 1, 0, st>>>(cstat, res);
+    nh_note_launch();
+  }
+  nh_free(cstat, st);
+  if (!rc) rc = run_peel(true, o, ri, s, cnt, core, round, uf, L, 0, 0.0, nullptr, res, st);
+  if (!rc) rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, res + 2, st);
+  return rc;
 }
 
 extern "C" int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L, const int32_t* pairs,

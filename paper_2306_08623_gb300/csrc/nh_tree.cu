@@ -52,14 +52,10 @@ __global__ void k_tree_write(int64_t n_r, const int32_t* __restrict__ uf, const 
 
 }  // namespace
 
-extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
-                                 uint32_t* label, int64_t* n_nodes, void* stream) {
-  if (n_r < 0 || (n_r > 0 && (!core || !uf || !L || !parent || !label)) || n_r >= (1ll << 31)) return NH_ERR_INVALID;
-  if (n_r == 0) {
-    if (n_nodes) *n_nodes = 0;
-    return NH_OK;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
+// Stream-ordered construct-tree: launches only; the node count lands in the device word
+// n_nodes_dev.  n_r >= 1, arguments checked by the caller.
+int nh_tree_enqueue(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
+                    uint32_t* label, int64_t* n_nodes_dev, cudaStream_t st) {
   uint32_t *own = nullptr, *nch = nullptr, *flag = nullptr;
   int64_t* nid = nullptr;
   int rc = NH_OK;
@@ -78,14 +74,31 @@ extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf,
   k_tree_flags<<<blocks, 256, 0, st>>>(n_r, uf, own, nch, flag);
   nh_note_launch();
   rc = nh_exclusive_scan_u32(flag, nid, n_r, st);
-  int64_t nn = 0;
   if (!rc) {
     k_tree_write<<<blocks, 256, 0, st>>>(n_r, uf, L, core, flag, nid, parent, label);
     nh_note_launch();
-    cudaMemcpyAsync(&nn, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(n_nodes_dev, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
   }
   if (cudaGetLastError() != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   nh_free(own, st); nh_free(nch, st); nh_free(flag, st); nh_free(nid, st);
+  return rc;
+}
+
+extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
+                                 uint32_t* label, int64_t* n_nodes, void* stream) {
+  if (n_r < 0 || (n_r > 0 && (!core || !uf || !L || !parent || !label)) || n_r >= (1ll << 31)) return NH_ERR_INVALID;
+  if (n_r == 0) {
+    if (n_nodes) *n_nodes = 0;
+    return NH_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t* nn_dev = nullptr;
+  int rc = nh_alloc(&nn_dev, 1, st);
+  if (rc) return rc;
+  rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, nn_dev, st);
+  int64_t nn = 0;
+  if (!rc) cudaMemcpyAsync(&nn, nn_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  nh_free(nn_dev, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (!rc && n_nodes) *n_nodes = nn;
   return rc;

@@ -61,6 +61,7 @@ def lib():
             "nh_construct_tree": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_hierarchy_two_phase": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
+            "nh_hierarchy_enqueue": (I32, [P, P, I32, P, P, P, P, P, P, P, P, P]),
             "nh_set_peel_max_group": (I32, [I32]),
             "nh_set_peel_task_items": (I32, [I32]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
@@ -220,6 +221,24 @@ def hierarchy_two_phase(o: Oriented, ri: RIndex, s: int, core: torch.Tensor, str
 
 
 TREE_NOALLOC_MAX = 1 << 18
+
+
+def hierarchy_buffers(ri: RIndex) -> dict:
+    """Device outputs of hierarchy_enqueue for one r-clique index."""
+    n = max(ri.n_r, 1)
+    i32 = dict(dtype=torch.int32, device="cuda")
+    return {"cnt": torch.empty(n, **i32), "core": torch.empty(n, **i32), "round": torch.empty(n, **i32),
+            "uf": torch.empty(n, **i32), "L": torch.empty(n, **i32), "parent": torch.empty(2 * n, **i32),
+            "label": torch.empty(n, **i32), "res": torch.zeros(4, dtype=torch.int64, device="cuda")}
+
+
+def hierarchy_enqueue(o: Oriented, ri: RIndex, s: int, buf: dict, stream=None):
+    """Counts, peel with link-efficient and construct-tree in stream order with no host
+    synchronisation (capturable into a CUDA graph); buf from hierarchy_buffers.  After the stream
+    has run it, buf["res"] holds (status, n_s, n_nodes, rounds)."""
+    _check("nh_hierarchy_enqueue", lib().nh_hierarchy_enqueue(
+        o.handle, ri.handle, s, _dptr(buf["cnt"]), _dptr(buf["core"]), _dptr(buf["round"]), _dptr(buf["uf"]),
+        _dptr(buf["L"]), _dptr(buf["parent"]), _dptr(buf["label"]), _dptr(buf["res"]), _stream(stream)))
 
 
 def construct_tree_noalloc(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent: torch.Tensor,
