@@ -324,7 +324,7 @@ def run_ours(args):
         with open(tpath) as f:
             tt = json.load(f)
         if (tt.get("kernel") == "k_peel<%d,%d,true>" % dom and tt.get("method") == METHOD[dom]
-                and tt.get("source_hash") == _source_hash()):
+                and tt.get("source_hash") == _source_hash(dom)):
             traffic = tt.get("dram_bytes_per_launch")
 
     # end to end through host buffers: H2D of the CSR from pinned memory, the path, D2H of
@@ -592,11 +592,15 @@ def run_approx(args):
     print(json.dumps(line), flush=True)
 
 
-def _source_hash() -> str:
+def _source_hash(pair) -> str:
+    """Hash of the sources the peel kernel of one (r,s) pair is compiled from (a traffic record
+    counts only for the kernel it was taken on)."""
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2306_08623_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2306_08623_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2306_08623_gb300", "csrc")
+    for path in (os.path.join(csrc, "nh_peel.cuh"), os.path.join(csrc, "nh_internal.cuh"),
+                 os.path.join(csrc, "nh_peel_rs%d%d.cu" % pair), os.path.join(ROOT, "include", "nucleus.h")):
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
