@@ -75,6 +75,8 @@ def _load():
         lib.orc_nucleus.restype = ctypes.POINTER(_Result)
         lib.orc_nucleus.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_double]
+        lib.orc_label_hierarchy.restype = ctypes.POINTER(_Result)
+        lib.orc_label_hierarchy.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int, P]
         lib.orc_tree_from_uf.restype = ctypes.POINTER(_Result)
         lib.orc_tree_from_uf.argtypes = [ctypes.c_int64, P, P, P]
         lib.orc_free.argtypes = [ctypes.POINTER(_Result)]
@@ -161,6 +163,31 @@ def nucleus(off, adj, r: int, s: int, core: bool = True, hier: str | None = "def
             out["approx_T"] = int(res.approx_T)
             out["thresholds"] = _copy(res.thresholds, res.n_thresholds, np.uint32)
         return out
+    finally:
+        lib.orc_free(p)
+
+
+def label_hierarchy(off, adj, r: int, s: int, labels) -> dict:
+    """Definitional hierarchy of arbitrary per-r-clique labels (lexicographic ids): leaf_node,
+    node_parent, node_label, n_nodes (plus n_r, n_s, cnt)."""
+    off, adj = _csr(off, adj)
+    labels = np.ascontiguousarray(labels, dtype=np.uint32)
+    lib = _load()
+    n_r = lib.orc_count_cliques(len(off) - 1, _ptr(off), _ptr(adj), r)
+    if len(labels) != n_r:
+        raise ValueError("labels must have one entry per r-clique (%d), got %d" % (n_r, len(labels)))
+    p = lib.orc_label_hierarchy(len(off) - 1, _ptr(off), _ptr(adj), r, s, _ptr(labels))
+    if not p:
+        raise MemoryError("oracle allocation failed")
+    try:
+        res = p.contents
+        if res.status != 0:
+            raise RuntimeError("oracle failed with status %d" % res.status)
+        nn = res.n_nodes
+        return {"n_r": res.n_r, "n_s": res.n_s, "cnt": _copy(res.cnt, res.n_r, np.uint32), "n_nodes": nn,
+                "leaf_node": _copy(res.leaf_node, res.n_r, np.int32),
+                "node_parent": _copy(res.node_parent, nn, np.int32),
+                "node_label": _copy(res.node_label, nn, np.uint32)}
     finally:
         lib.orc_free(p)
 

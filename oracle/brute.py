@@ -66,7 +66,27 @@ def brute_nucleus(n: int, edges, r: int, s: int, mode: str = "def"):
     for lev in range(1, kmax + 1):
         for x in X[lev]:
             core[x] = lev
-    # components per level
+    nodes = components_by_level(n_r, mem, core, kmax, mode)
+    return {"rcliques": rcl, "n_s": len(scl), "cnt": cnt, "core": core, "kmax": kmax, "nodes": nodes}
+
+
+def brute_label_hierarchy(n: int, edges, r: int, s: int, labels) -> dict[frozenset, int]:
+    """Hierarchy nodes of arbitrary per-r-clique labels (lexicographic r-clique ids), by the same
+    definition with labels in place of core numbers."""
+    adjset = [set() for _ in range(n)]
+    for a, b in edges:
+        adjset[a].add(b)
+        adjset[b].add(a)
+    rcl = cliques(n, adjset, r)
+    rid = {c: i for i, c in enumerate(rcl)}
+    mem = [[rid[sub] for sub in combinations(S, r)] for S in cliques(n, adjset, s)]
+    labels = [int(x) for x in labels]
+    return components_by_level(len(rcl), mem, labels, max(labels, default=0), "def")
+
+
+def components_by_level(n_r: int, mem, core, kmax: int, mode: str) -> dict[frozenset, int]:
+    """Every component of size >= 2 at every level c >= 1 (r-cliques of core >= c, joined by the
+    s-cliques inside), labelled by the largest c at which it is a component."""
     nodes: dict[frozenset, int] = {}
     for lev in range(1, kmax + 1):
         par = list(range(n_r))
@@ -94,7 +114,7 @@ def brute_nucleus(n: int, edges, r: int, s: int, mode: str = "def"):
             if len(comp) >= 2:
                 fs = frozenset(comp)
                 nodes[fs] = max(nodes.get(fs, 0), lev)
-    return {"rcliques": rcl, "n_s": len(scl), "cnt": cnt, "core": core, "kmax": kmax, "nodes": nodes}
+    return nodes
 
 
 def tree_to_nodes(leaf_node, node_parent, node_label) -> dict[frozenset, int]:

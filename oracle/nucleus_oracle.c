@@ -290,10 +290,13 @@ static int64_t uf_find(int64_t* p, int64_t x) {
 }
 
 /* Union edges (a,b,level): a and b are joined at every level <= level.  Processes levels from
- * kmax down to 1 with one union-find; at level c a new node is made for every component that
- * holds an r-clique of core exactly c (components made only of higher-core r-cliques are
- * unchanged from level c+1).  The new node adopts the current top nodes of the components it
- * absorbed. */
+ * kmax down to 1 with one union-find; at level c a new node is made for every component of at
+ * least two r-cliques that holds an r-clique of label exactly c (components made only of
+ * higher-label r-cliques are unchanged from level c+1).  The new node adopts the current top
+ * nodes of the components it absorbed.  An r-clique still alone at its own level (possible for
+ * labels that are not core numbers, never for core numbers, since an r-clique of core c >= 1
+ * lies in an s-clique of the c-nucleus) waits in its component's pending list and becomes a leaf
+ * of the first node its component gets at a lower level (or of none). */
 static int hierarchy_by_levels(int64_t n_r, const uint32_t* core, uint32_t kmax,
                                const int64_t* lvl_off, const int32_t* ea, const int32_t* eb,
                                orc_result* res) {
@@ -306,17 +309,21 @@ static int hierarchy_by_levels(int64_t n_r, const uint32_t* core, uint32_t kmax,
   int64_t* pnext = malloc(sizeof(int64_t) * (n_r ? n_r : 1));
   int64_t* by_core_off = calloc((size_t)kmax + 2, sizeof(int64_t));
   int64_t* by_core = malloc(sizeof(int64_t) * (n_r ? n_r : 1));
+  int64_t* ph = malloc(sizeof(int64_t) * (n_r ? n_r : 1));   /* pending list head / tail per root */
+  int64_t* pt = malloc(sizeof(int64_t) * (n_r ? n_r : 1));
+  int64_t* pn = malloc(sizeof(int64_t) * (n_r ? n_r : 1));   /* next pending r-clique */
   res->leaf_node = malloc(sizeof(int32_t) * (n_r ? n_r : 1));
   res->node_parent = malloc(sizeof(int32_t) * (n_r ? n_r : 1));
   res->node_label = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
   if (!par || !sz || !head || !tail || !stamp_node || !stamp_lvl || !pnext || !by_core_off || !by_core ||
-      !res->leaf_node || !res->node_parent || !res->node_label) {
+      !ph || !pt || !pn || !res->leaf_node || !res->node_parent || !res->node_label) {
     free(par); free(sz); free(head); free(tail); free(stamp_node); free(stamp_lvl); free(pnext);
-    free(by_core_off); free(by_core);
+    free(by_core_off); free(by_core); free(ph); free(pt); free(pn);
     return ORC_ERR_NOMEM;
   }
   for (int64_t i = 0; i < n_r; i++) {
     par[i] = i; sz[i] = 1; head[i] = tail[i] = -1; stamp_lvl[i] = 0; stamp_node[i] = -1;
+    ph[i] = pt[i] = pn[i] = -1;
     res->leaf_node[i] = -1;
   }
   for (int64_t i = 0; i < n_r; i++) by_core_off[core[i] + 1]++;
@@ -340,10 +347,20 @@ static int hierarchy_by_levels(int64_t n_r, const uint32_t* core, uint32_t kmax,
         else { pnext[tail[a]] = head[b]; tail[a] = tail[b]; }
         head[b] = tail[b] = -1;
       }
+      if (ph[b] >= 0) {
+        if (ph[a] < 0) { ph[a] = ph[b]; pt[a] = pt[b]; }
+        else { pn[pt[a]] = ph[b]; pt[a] = pt[b]; }
+        ph[b] = pt[b] = -1;
+      }
     }
     for (int64_t q = by_core_off[c]; q < by_core_off[c + 1]; q++) {
       int64_t R = by_core[q];
       int64_t root = uf_find(par, R);
+      if (sz[root] == 1) {  /* alone at its own level: pending */
+        if (ph[root] < 0) { ph[root] = R; pt[root] = R; }
+        else { pn[pt[root]] = R; pt[root] = R; }
+        continue;
+      }
       if (stamp_lvl[root] != c || stamp_node[root] < 0) {
         int64_t N = nn++;
         res->node_label[N] = c;
@@ -355,12 +372,14 @@ static int hierarchy_by_levels(int64_t n_r, const uint32_t* core, uint32_t kmax,
         stamp_node[root] = N;
       }
       res->leaf_node[R] = (int32_t)stamp_node[root];
+      for (int64_t x = ph[root]; x >= 0; x = pn[x]) res->leaf_node[x] = (int32_t)stamp_node[root];
+      ph[root] = pt[root] = -1;
     }
     if (c == 1) break;
   }
   res->n_nodes = nn;
   free(par); free(sz); free(head); free(tail); free(stamp_node); free(stamp_lvl); free(pnext);
-  free(by_core_off); free(by_core);
+  free(by_core_off); free(by_core); free(ph); free(pt); free(pn);
   return ORC_OK;
 }
 
@@ -674,8 +693,8 @@ enum { ORC_HIER_NONE = 0, ORC_HIER_DEF = 1, ORC_HIER_PAIR = 2, ORC_HIER_LINK_DEF
 
 /* Full sequential run on an undirected simple graph in CSR form (sorted lists, no loops or
  * duplicates).  flags: ORC_WANT_CORE | ORC_WANT_APPROX; hier_mode selects the hierarchy. */
-orc_result* orc_nucleus(int64_t n, const int64_t* off, const int32_t* adj, int r, int s, int flags,
-                        int hier_mode, double delta) {
+static orc_result* nucleus_impl(int64_t n, const int64_t* off, const int32_t* adj, int r, int s, int flags,
+                                int hier_mode, double delta, const uint32_t* labels) {
   orc_result* res = calloc(1, sizeof(orc_result));
   if (!res) return NULL;
   res->r = r; res->s = s;
@@ -719,7 +738,15 @@ orc_result* orc_nucleus(int64_t n, const int64_t* off, const int32_t* adj, int r
     free(fill);
   }
 
-  if ((flags & ORC_WANT_CORE) || hier_mode != ORC_HIER_NONE) {
+  if (labels) {  /* the hierarchy of given labels in place of core numbers */
+    res->core = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
+    if (!res->core) { res->status = ORC_ERR_NOMEM; goto done; }
+    res->kmax = 0;
+    for (int64_t R = 0; R < n_r; R++) {
+      res->core[R] = labels[R];
+      if (labels[R] > res->kmax) res->kmax = labels[R];
+    }
+  } else if ((flags & ORC_WANT_CORE) || hier_mode != ORC_HIER_NONE) {
     res->core = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
     if (!res->core) { res->status = ORC_ERR_NOMEM; goto done; }
     res->status = exact_peel(n_r, res->cnt, inc_off, inc, mc.members, C, n_s, res->core, &res->kmax);
@@ -744,6 +771,22 @@ orc_result* orc_nucleus(int64_t n, const int64_t* off, const int32_t* adj, int r
 done:
   free(mc.members); free(inc_off); free(inc);
   return res;
+}
+
+orc_result* orc_nucleus(int64_t n, const int64_t* off, const int32_t* adj, int r, int s, int flags,
+                        int hier_mode, double delta) {
+  return nucleus_impl(n, off, adj, r, s, flags, hier_mode, delta, NULL);
+}
+
+/* The definitional hierarchy (§3) of arbitrary per-r-clique labels (lexicographic r-clique ids)
+ * instead of core numbers: at level c the r-cliques of label >= c are joined through every
+ * s-clique whose members all have label >= c; nodes are the components of at least two
+ * r-cliques, labelled by the highest level at which they exist (= their least member label).
+ * With core numbers as labels this is the core hierarchy; with the approximate values of
+ * Alg. 2 it is the approximate hierarchy of §6 (which applies Alg. 1 to approximate values). */
+orc_result* orc_label_hierarchy(int64_t n, const int64_t* off, const int32_t* adj, int r, int s,
+                                const uint32_t* labels) {
+  return nucleus_impl(n, off, adj, r, s, 0, ORC_HIER_DEF, 0.0, labels);
 }
 
 /* ------------------------------------------------------------------------------------------ */

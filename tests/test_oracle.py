@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle.brute import brute_nucleus, tree_to_nodes
+from oracle.brute import brute_label_hierarchy, brute_nucleus, tree_to_nodes
 from paper_2306_08623_gb300 import graphgen as gg
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -390,3 +390,55 @@ def test_check_sample_accepts_truth_and_rejects_planted_mistakes():
         parent2[n_r + child] = -1
         assert oracle.check_sample(off, adj, r, s, tuples, sample, core=res["core"], parent=parent2,
                                    label=label)[3] >= 1
+
+
+# ---- hierarchy of arbitrary labels (the approximate hierarchy of §6 on Alg. 2's values) ----
+
+def _edges(off, adj):
+    return [(a, int(b)) for a in range(len(off) - 1) for b in adj[off[a]:off[a + 1]] if a < b]
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (1, 3), (2, 3), (2, 4), (3, 4)])
+def test_label_hierarchy_vs_brute_force(r, s):
+    """Core numbers, random labels (r-cliques left alone at their own level occur) and Alg. 2's
+    approximate values, against components taken level by level from the definition."""
+    rng = np.random.default_rng(100 + 10 * r + s)
+    n_cases = 0
+    for _ in range(60):
+        n = int(rng.integers(4, 10))
+        off, adj = gg.gnp(n, float(rng.uniform(0.4, 0.95)), int(rng.integers(1 << 30)))
+        o = oracle.nucleus(off, adj, r, s)
+        if o["n_r"] == 0:
+            continue
+        for lab in (o["core"], rng.integers(0, 6, size=o["n_r"]).astype(np.uint32),
+                    oracle.nucleus(off, adj, r, s, hier=None, approx_delta=0.5)["approx"]):
+            res = oracle.label_hierarchy(off, adj, r, s, lab)
+            got = tree_to_nodes(res["leaf_node"], res["node_parent"], res["node_label"])
+            assert got == brute_label_hierarchy(n, _edges(off, adj), r, s, lab)
+            n_cases += 1
+    assert n_cases > 100
+
+
+def test_label_hierarchy_of_cores_is_the_core_hierarchy():
+    off, adj = gg.rmat(8, 8, 3)
+    for r, s in [(1, 2), (2, 3), (2, 4), (3, 4)]:
+        o = oracle.nucleus(off, adj, r, s)
+        res = oracle.label_hierarchy(off, adj, r, s, o["core"])
+        assert tree_to_nodes(res["leaf_node"], res["node_parent"], res["node_label"]) == \
+            tree_to_nodes(o["leaf_node"], o["node_parent"], o["node_label"])
+
+
+def test_label_hierarchy_singleton_waits_for_a_lower_level():
+    """K3 with (1,2): vertex 0 labelled 2, the others 1.  At level 2 vertex 0 is alone (no edge
+    has both ends labelled >= 2), so no node exists there; at level 1 all three join: one node
+    {0,1,2} labelled 1, and vertex 0 is its leaf."""
+    off, adj = gg.complete(3)
+    res = oracle.label_hierarchy(off, adj, 1, 2, np.array([2, 1, 1], dtype=np.uint32))
+    assert res["n_nodes"] == 1
+    assert list(res["leaf_node"]) == [0, 0, 0]
+    assert list(res["node_label"]) == [1]
+    # a vertex whose label is never matched by any edge stays outside every node
+    off, adj = gg.from_edges(4, [(0, 1), (1, 2)])
+    res = oracle.label_hierarchy(off, adj, 1, 2, np.array([0, 3, 3, 5], dtype=np.uint32))
+    assert tree_to_nodes(res["leaf_node"], res["node_parent"], res["node_label"]) == {frozenset({1, 2}): 3}
+    assert res["leaf_node"][0] == -1 and res["leaf_node"][3] == -1
