@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
-    ap.add_argument("--workload", choices=["rmat18", "cl4m", "batch512", "approx", "peel1"], default="rmat18",
+    ap.add_argument("--workload", choices=["rmat18", "cl4m", "batch512", "approx", "approx_hier", "peel1"],
+                    default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
                          "exact core numbers on R-MAT 22 (2,3) and R-MAT 20 (3,4); peel1: one exact hierarchy of "
@@ -543,6 +544,51 @@ def run_peel1(args):
     print(json.dumps(line), flush=True)
 
 
+def run_approx_hier(args):
+    """Approximate hierarchy (the definitional hierarchy of Alg. 2's values) beside the exact one,
+    on R-MAT 18 EF16 seed 2, (2,3) and (3,4), delta in {0.1, 0.5}: peel and hierarchy times and
+    node counts (one warm-up run of each, then one timed run)."""
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    off, adj = gg.rmat(18, 16, 2)
+    o = nc.build_orientation(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda())
+    out = {}
+    for r, s in [(2, 3), (3, 4)]:
+        ri = nc.index_r_cliques(o, r)
+        cnt, n_s = nc.count_s_cliques(o, ri, s)
+        entry = {"n_r": ri.n_r, "n_s": n_s}
+        for rep in range(2):
+            a = _ev()
+            pk = nc.peel_cores(o, ri, s, cnt)
+            b = _ev()
+            _, _, nn = nc.label_hierarchy(o, ri, s, pk["core"])
+            c = _ev()
+            entry["exact"] = {"peel_ms": _ms(a, b), "hierarchy_ms": _ms(b, c), "nodes": nn}
+            del pk
+        for delta in (0.1, 0.5):
+            for rep in range(2):
+                a = _ev()
+                ap = nc.approx_nucleus(o, ri, s, delta, cnt, stats=True)
+                b = _ev()
+                _, _, nn = nc.label_hierarchy(o, ri, s, ap["approx"])
+                c = _ev()
+                entry["delta_%g" % delta] = {"peel_ms": _ms(a, b), "hierarchy_ms": _ms(b, c), "nodes": nn,
+                                             "rounds": ap["stats"]["rounds"]}
+                del ap
+        out["RMAT18 (%d,%d)" % (r, s)] = entry
+    e = out["RMAT18 (2,3)"]
+    tot_exact = e["exact"]["peel_ms"] + e["exact"]["hierarchy_ms"]
+    tot_apx = e["delta_0.1"]["peel_ms"] + e["delta_0.1"]["hierarchy_ms"]
+    line = {"metric": "approximate vs exact hierarchy time", "value": tot_exact / tot_apx,
+            "unit": "x speedup (RMAT18 (2,3), delta 0.1, peel + hierarchy)", "higher_is_better": True,
+            "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "R-MAT 18 EF16 seed 2, (2,3) and (3,4)", "results": out}}
+    print(json.dumps(line), flush=True)
+
+
 def run_approx(args):
     """Approximate core numbers (Alg. 2) beside the exact GPU run: (2,3) on R-MAT 22 EF16 seed 4,
     (3,4) on R-MAT 20 EF16 seed 3, delta in {0.1, 0.5}: time, speedup over the exact peel, and the
@@ -616,6 +662,8 @@ def main():
         run_batch512(args)
     elif args.workload == "approx":
         run_approx(args)
+    elif args.workload == "approx_hier":
+        run_approx_hier(args)
     elif args.workload == "peel1":
         run_peel1(args)
     else:

@@ -149,6 +149,18 @@ int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, co
 int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
                            int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
+/* The definitional hierarchy (§3) of arbitrary labels in place of core numbers, by the same
+ * two-phase procedure: at level c the r-cliques of label >= c are joined through every s-clique
+ * whose members all have label >= c; a node is a component of at least two r-cliques, labelled
+ * with its least member label.  With the approximate values of nh_approx_nucleus as labels this
+ * is the approximate hierarchy of §6 (Alg. 1 applied to approximate values, read
+ * definitionally).  An r-clique in no s-clique whose members all reach its own label is alone at
+ * that level and becomes a leaf of the first node its component gets at a lower level (parent
+ * -1 if none).  labels: device uint32[n_r], every label <= 2^30 (NH_ERR_INVALID otherwise);
+ * parent / label / n_nodes as nh_construct_tree.  Synchronises the stream. */
+int nh_label_hierarchy(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* labels,
+                       int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
+
 /* a10 -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
  * x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta) (IEEE double, C = binom(s,r)); round t peels
  * every live r-clique with count <= t_i; after T = ceil(ln(max(n_r,2)) / log1p(delta/C)) + 1

@@ -366,8 +366,9 @@ __global__ void k_two_phase_init(int64_t n_r, int32_t* __restrict__ uf, uint32_t
 
 }  // namespace nhp
 
-extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
-                                      int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
+// label_mode: `core` holds arbitrary labels; r-cliques alone at their own level are handled
+static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core, int32_t* parent,
+                          uint32_t* label, int64_t* n_nodes, bool label_mode, void* stream) {
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
   if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
@@ -396,8 +397,14 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   unsigned long long* cursor = nullptr;
   int32_t* order = nullptr;
   uint32_t* cost = nullptr;
+  uint32_t* mark = nullptr;
   int rc = NH_OK;
   unsigned int kmax = 0;
+  if (label_mode) {
+    if ((rc = nh_alloc(&mark, n_r, st))) return rc;
+    cudaMemsetAsync(mark, 0, sizeof(uint32_t) * (size_t)n_r, st);
+    A.mark = mark;
+  }
   if ((rc = nh_alloc(&A.lk.uf, n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) || (rc = nh_alloc(&A.touched, (int64_t)A.touched_cap, st)) ||
       (rc = nh_alloc(&A.touched_n, 1, st)) || (rc = nh_alloc(&T.lvl, n_r, st)) || (rc = nh_alloc(&T.nid, n_r, st)) ||
       (rc = nh_alloc(&T.top, n_r, st)) || (rc = nh_alloc(&T.node_count, 1, st)) || (rc = nh_alloc(&dmax, 1, st)) ||
@@ -410,6 +417,7 @@ extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri,
   nh_note_launch();
   cudaMemcpyAsync(&kmax, dmax, sizeof(kmax), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
+  if (kmax > (1u << 30)) { rc = NH_ERR_INVALID; goto cleanup; }  // one histogram entry per level
   if ((rc = nh_alloc(&hist, (int64_t)kmax + 2, st)) || (rc = nh_alloc(&off, (int64_t)kmax + 3, st)) ||
       (rc = nh_alloc(&cursor, (int64_t)kmax + 2, st)))
     goto cleanup;
@@ -445,8 +453,19 @@ cleanup:
   nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
   nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
   nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(cost, st);
+  nh_free(mark, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
+}
+
+extern "C" int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core,
+                                      int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
+  return two_phase_impl(o, ri, s, core, parent, label, n_nodes, false, stream);
+}
+
+extern "C" int nh_label_hierarchy(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* labels,
+                                  int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream) {
+  return two_phase_impl(o, ri, s, labels, parent, label, n_nodes, true, stream);
 }
 
 extern "C" int nh_set_peel_max_group(int g) {

@@ -74,6 +74,7 @@ struct PeelArgs {
   int union_mode;         // two-phase hierarchy: re-listing unites instead of peeling
   int gmax;               // largest number of warps per frontier r-clique (power of two)
   const uint32_t* cost;   // chunks of 32 list entries per r-clique (work-proportional re-listing)
+  uint32_t* mark;         // label hierarchy: 1 for an r-clique in an s-clique at its own level
   unsigned int task_items;  // largest list re-listed in work-proportional tasks (<= kTaskItems)
   int32_t* touched;       // two-phase: roots joined at the current level
   unsigned long long* touched_n;
@@ -466,6 +467,7 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
       if (c == thr && mem[j] < attr) attr = mem[j];
     }
     ls.listed++;
+    if (A.mark && !__ldcg(A.mark + Rid)) __stcg(A.mark + Rid, 1u);  // least label over S is Rid's
     if (attr != Rid) return;
 #pragma unroll
     for (int j = 0; j < CM; j++) {
@@ -1117,9 +1119,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_two_phase(PeelArgs A, 
     relist_list<R, S, true>(A, T.order + lo, cnt, tasks, total, 0u, level, nullptr, lane, gwarp, nwarps, W, ls,
                             s_pref, &ctl->task_next);
     if (!grid_sync(ctl, A.timeout_ns, [&] { ctl->task_next = 0; })) break;
-    // a node for every component holding an r-clique of this level
+    // a node for every component holding an r-clique of this level (with labels that are not
+    // core numbers, an r-clique in no s-clique at its own level is alone there: no node; it
+    // becomes a leaf of the first node its component gets at a lower level, through the touched
+    // list below)
     for (long long i = gtid; i < (long long)cnt; i += nthreads) {
-      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
+      const int32_t R0 = T.order[lo + i];
+      if (A.mark && !__ldcg(A.mark + R0)) continue;
+      const int32_t y = uf_find(A.lk.uf, R0);
       uint32_t cur = __ldcg(T.lvl + y);
       while (cur != level) {
         const uint32_t prev = atomicCAS(T.lvl + y, cur, level);
@@ -1137,6 +1144,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_two_phase(PeelArgs A, 
     // leaves of this level, and previous top nodes of every joined component
     for (long long i = gtid; i < (long long)cnt; i += nthreads) {
       const int32_t R0 = T.order[lo + i];
+      if (A.mark && !__ldcg(A.mark + R0)) continue;
       T.parent[R0] = __ldcg(T.nid + uf_find(A.lk.uf, R0));
     }
     {
@@ -1145,11 +1153,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_two_phase(PeelArgs A, 
         const int32_t x = __ldcg(A.touched + i);
         const int32_t tp = __ldcg(T.top + x);
         if (tp >= 0) T.parent[n_r + tp] = __ldcg(T.nid + uf_find(A.lk.uf, x));
+        else if (A.mark) T.parent[x] = __ldcg(T.nid + uf_find(A.lk.uf, x));  // x was alone until now
       }
     }
     if (!grid_sync(ctl, A.timeout_ns, [&] { *A.touched_n = 0; })) break;
     for (long long i = gtid; i < (long long)cnt; i += nthreads) {
-      const int32_t y = uf_find(A.lk.uf, T.order[lo + i]);
+      const int32_t R0 = T.order[lo + i];
+      if (A.mark && !__ldcg(A.mark + R0)) continue;
+      const int32_t y = uf_find(A.lk.uf, R0);
       T.top[y] = __ldcg(T.nid + y);
     }
     if (!grid_sync(ctl, A.timeout_ns, [] {})) break;

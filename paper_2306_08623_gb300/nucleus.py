@@ -62,6 +62,7 @@ def lib():
             "nh_construct_tree_noalloc": (I32, [I64, P, P, P, P, P, ctypes.POINTER(I64), P]),
             "nh_hierarchy_two_phase": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
             "nh_hierarchy_enqueue": (I32, [P, P, I32, P, P, P, P, P, P, P, P, P]),
+            "nh_label_hierarchy": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
             "nh_set_peel_max_group": (I32, [I32]),
             "nh_set_peel_task_items": (I32, [I32]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
@@ -221,6 +222,18 @@ def hierarchy_two_phase(o: Oriented, ri: RIndex, s: int, core: torch.Tensor, str
 
 
 TREE_NOALLOC_MAX = 1 << 18
+
+
+def label_hierarchy(o: Oriented, ri: RIndex, s: int, labels: torch.Tensor, stream=None):
+    """Definitional hierarchy of arbitrary labels (e.g. approx_nucleus values: the approximate
+    hierarchy); returns (parent, label, n_nodes) like construct_tree."""
+    n_r = ri.n_r
+    parent = torch.empty(max(2 * n_r, 1), dtype=torch.int32, device="cuda")
+    label = torch.empty(max(n_r, 1), dtype=torch.int32, device="cuda")
+    nn = I64()
+    _check("nh_label_hierarchy", lib().nh_label_hierarchy(o.handle, ri.handle, s, _dptr(labels), _dptr(parent),
+                                                          _dptr(label), ctypes.byref(nn), _stream(stream)))
+    return parent[: n_r + nn.value], label[: nn.value], nn.value
 
 
 def hierarchy_buffers(ri: RIndex) -> dict:
