@@ -383,25 +383,40 @@ def set_peel_task_items(n: int):
     _check("nh_set_peel_task_items", lib().nh_set_peel_task_items(int(n)))
 
 
-def autotune_peel_max_group(run, candidates=(16, 64, 256, 1024), repeats: int = 1) -> dict:
-    """Time `run()` (a callable doing one timed piece of work on the device) under each
-    candidate warps-per-r-clique cap; keep the fastest cap set and return all timings (ms)."""
+def _cuda_timer(run) -> float:
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    run()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def autotune_peel(run, max_groups=(16, 64, 256, 1024), task_items=(-1,), repeats: int = 1,
+                  timer=None) -> dict:
+    """Grid search over the peel's scheduling knobs: time `run()` (one piece of device work, e.g.
+    a whole hierarchy) under every (warps-per-r-clique cap, task-frontier size) pair, keep the
+    fastest pair set, and return {"best": (cap, items), "times_ms": {(cap, items): ms}}.  The knobs
+    change only the scheduling, never a result.  `timer(run) -> ms` defaults to CUDA events on
+    the current stream."""
+    timer = timer or _cuda_timer
     times = {}
-    for g in candidates:
-        set_peel_max_group(g)
-        best = None
-        for _ in range(repeats):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            run()
-            b.record()
-            b.synchronize()
-            t = a.elapsed_time(b)
-            best = t if best is None else min(best, t)
-        times[g] = best
-    set_peel_max_group(min(times, key=times.get))
-    return times
+    for g in max_groups:
+        for t in task_items:
+            set_peel_max_group(g)
+            set_peel_task_items(t)
+            times[(g, t)] = min(timer(run) for _ in range(max(1, repeats)))
+    best = min(times, key=times.get)
+    set_peel_max_group(best[0])
+    set_peel_task_items(best[1])
+    return {"best": best, "times_ms": times}
+
+
+def autotune_peel_max_group(run, candidates=(16, 64, 256, 1024), repeats: int = 1, timer=None) -> dict:
+    """autotune_peel over the warps-per-r-clique cap alone; returns {cap: ms}."""
+    res = autotune_peel(run, max_groups=candidates, task_items=(-1,), repeats=repeats, timer=timer)
+    return {g: ms for (g, _), ms in res["times_ms"].items()}
 
 
 def kernel_launches() -> int:
