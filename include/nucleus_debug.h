@@ -1,0 +1,33 @@
+/* nucleus_debug.h -- fault injection for tests of libnucleus's error paths.
+ *
+ * Host-side settings only (process-wide, not thread-safe; set them between calls).  Nothing here
+ * makes a GPU fault, trap or hang: a shortened wait limit makes the persistent kernels' bounded
+ * grid barriers give up early, every block then leaves its loop and the call returns
+ * NH_ERR_TIMEOUT with the context intact; a forced hash-table capacity makes the (bounded)
+ * insertion run out of slots and the call returns NH_ERR_TABLE_FULL.  Status codes are those of
+ * nucleus.h. */
+#ifndef NUCLEUS_DEBUG_H
+#define NUCLEUS_DEBUG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* wait limit, in ns, of the grid barriers of the peel (nh_peel_and_link, nh_approx_nucleus,
+ * nh_hierarchy_enqueue) and of the two-phase / label hierarchies; 0 = the default (60 s) */
+#define NH_INJECT_WAIT_NS 1
+/* capacity, in slots (a power of two), of the edge table (nh_build_orientation) and of the
+ * triangle table (nh_index_r_cliques, r = 3) built from now on; 0 = automatic (load <= 0.5) */
+#define NH_INJECT_TABLE_CAP 2
+
+/* Set one injection.  value >= 0 (NH_INJECT_TABLE_CAP: 0 or a power of two).  Returns NH_OK or
+ * NH_ERR_INVALID (unknown `what`, bad value; nothing changed). */
+int nh_debug_inject(int what, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -2,6 +2,7 @@
 #include <atomic>
 
 #include "nh_internal.cuh"
+#include "nucleus_debug.h"
 
 static std::atomic<long long> g_launches{0};
 
@@ -25,3 +26,21 @@ extern "C" const char* nh_status_string(int status) {
 }
 
 extern "C" int nh_version(void) { return 100; }
+
+// fault injection (include/nucleus_debug.h); read by the drivers in nh_peel.cu and nh_orient.cu
+long long g_nh_inject_wait_ns = 0;
+long long g_nh_inject_table_cap = 0;
+
+extern "C" int nh_debug_inject(int what, int64_t value) {
+  if (value < 0) return NH_ERR_INVALID;
+  if (what == NH_INJECT_WAIT_NS) {
+    g_nh_inject_wait_ns = (long long)value;
+    return NH_OK;
+  }
+  if (what == NH_INJECT_TABLE_CAP) {
+    if (value != 0 && (value & (value - 1))) return NH_ERR_INVALID;
+    g_nh_inject_table_cap = (long long)value;
+    return NH_OK;
+  }
+  return NH_ERR_INVALID;
+}

@@ -1,6 +1,8 @@
 // nh_orient.cu -- a1 (Arb-Orient: degree orientation + canonical edge ids) and a2 (r-clique index).
 #include "nh_internal.cuh"
 
+extern long long g_nh_inject_table_cap;  // fault injection (nh_api.cu): forced table capacity
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -382,6 +384,7 @@ extern "C" int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, 
   {
     unsigned long long cap = 1024;
     while (cap < 2ull * (unsigned long long)m) cap <<= 1;
+    if (g_nh_inject_table_cap > 0) cap = (unsigned long long)g_nh_inject_table_cap;
     int* status = nullptr;
     if ((rc = nh_alloc(&o->ekey, (int64_t)cap, st)) || (rc = nh_alloc(&o->eval, (int64_t)cap, st)) ||
         (rc = nh_alloc(&status, 1, st))) {
@@ -450,6 +453,7 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
     if (!rc && ntri >= (1ll << 32) - 1) rc = NH_ERR_UNSUPPORTED;
     unsigned long long cap = 1024;
     while (cap < 2ull * (unsigned long long)ntri) cap <<= 1;
+    if (g_nh_inject_table_cap > 0) cap = (unsigned long long)g_nh_inject_table_cap;
     if (!rc) rc = nh_alloc(&ri->tri, 3 * ntri, st);
     if (!rc) rc = nh_alloc(&ri->table, (int64_t)cap, st);
     if (!rc) {

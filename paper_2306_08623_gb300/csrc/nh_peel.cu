@@ -25,6 +25,7 @@
 
 #include "nh_peel.cuh"
 
+extern long long g_nh_inject_wait_ns;  // fault injection (nh_api.cu): grid-barrier wait limit
 static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
 static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
 
@@ -157,7 +158,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   // over many warps repeats walks; for s - r = 1 that costs more than the balance gains
   A.task_items = (unsigned int)(g_peel_task_items >= 0 ? g_peel_task_items
                                 : (exact && link_mode < 2 && s - r == 1) ? 0 : kTaskItems);
-  A.timeout_ns = 60ull * 1000000000ull;
+  A.timeout_ns = g_nh_inject_wait_ns > 0 ? (unsigned long long)g_nh_inject_wait_ns : 60ull * 1000000000ull;
   A.lk.uf = uf;
   A.lk.L = L;
   A.lk.core = val;
@@ -389,7 +390,7 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   A.task_items = (unsigned int)(g_peel_task_items >= 0 ? g_peel_task_items : kTaskItems);
   A.link_mode = -1;
   A.stats = 0;
-  A.timeout_ns = 60ull * 1000000000ull;
+  A.timeout_ns = g_nh_inject_wait_ns > 0 ? (unsigned long long)g_nh_inject_wait_ns : 60ull * 1000000000ull;
   A.touched_cap = 2ull * (unsigned long long)n_r + 64;
   unsigned int* dmax = nullptr;
   uint32_t* hist = nullptr;

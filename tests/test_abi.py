@@ -11,9 +11,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "nucleus.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(nh_[a-z_0-9]+)\s*\(", txt)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(nh_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -47,3 +51,19 @@ def test_oracle_shares_no_code_with_the_cuda_path():
             txt = open(p).read()
             assert "paper_2306_08623_gb300" not in txt.replace("paper_2306_08623_gb300/", "") or f == "__init__.py"
             assert "nucleus.h" not in txt and "libnucleus" not in txt
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="nvcc not available")
+def test_debug_injection_validates_its_arguments():
+    """nucleus_debug.h: host-side settings only (no GPU needed to set them)."""
+    from paper_2306_08623_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.nh_debug_inject.argtypes = [ctypes.c_int, ctypes.c_int64]
+    assert lib.nh_debug_inject(1, 1000) == 0
+    assert lib.nh_debug_inject(1, 0) == 0
+    assert lib.nh_debug_inject(2, 64) == 0
+    assert lib.nh_debug_inject(2, 0) == 0
+    assert lib.nh_debug_inject(2, 48) == 1   # not a power of two
+    assert lib.nh_debug_inject(1, -5) == 1
+    assert lib.nh_debug_inject(9, 1) == 1
