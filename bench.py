@@ -174,6 +174,24 @@ def run_reference(args):
 # our arm
 # -------------------------------------------------------------------------------------------------
 
+def pair_report(info: dict, peel_ms: dict, hier_ms: dict, alt_ms: dict, peak_gbs: float) -> dict:
+    """Per (r,s) pair of one step: sizes, the hierarchy builder, peel and hierarchy times, the
+    other builder's time, s-cliques peeled per second and the peel's algorithmic GB/s and
+    fraction of the HBM peak (every s-clique dies exactly once in the peel)."""
+    out = {}
+    for k, v in info.items():
+        other = "te" if METHOD[k] == "el" else "el"
+        gbs = algorithmic_peel_bytes(v["stats"], *k) / (peel_ms[k] / 1000.0) / 1e9 if peel_ms[k] > 0 else 0.0
+        out["%d,%d" % k] = {
+            "n_r": v["n_r"], "n_s": v["n_s"], "nodes": v["n_nodes"], "rounds": v["stats"]["rounds"],
+            "method": METHOD[k], "peel_ms": round(peel_ms[k], 3), "hierarchy_ms": round(hier_ms[k], 3),
+            other + "_peel_and_hierarchy_ms": round(alt_ms[k], 3),
+            "s_cliques_peeled_per_s": v["n_s"] / (peel_ms[k] / 1000.0) if peel_ms[k] > 0 else 0.0,
+            "peel_algorithmic_gbs": round(gbs, 3), "peel_frac_of_hbm_peak": gbs / peak_gbs,
+        }
+    return out
+
+
 def algorithmic_peel_bytes(stats: dict, r: int, s: int) -> int:
     """Bytes the peel must move, from its own counters: every scanned adjacency entry (4 B), the
     round stamps of the other members of every re-listed s-clique (4 B each), every count
@@ -365,12 +383,7 @@ def run_ours(args):
                          "(%d of %d cores), %.1f s" % (1, os.cpu_count() or 0, dt)}
 
     if rank == 0:
-        per_pair = {"%d,%d" % k: {"n_r": v["n_r"], "n_s": v["n_s"], "nodes": v["n_nodes"],
-                                  "rounds": v["stats"]["rounds"], "method": METHOD[k],
-                                  "peel_ms": round(peel_ms[k], 3), "hierarchy_ms": round(hier_ms[k], 3),
-                                  ("te" if METHOD[k] == "el" else "el") + "_peel_and_hierarchy_ms":
-                                      round(alt_ms[k], 3)}
-                    for k, v in info.items()}
+        per_pair = pair_report(info, peel_ms, hier_ms, alt_ms, peak)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

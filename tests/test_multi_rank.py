@@ -42,3 +42,18 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.reduce_max(42.0) == 42.0
     assert bench.whole_job_rate(10, 1, 3, 1000.0) == pytest.approx(30.0)
+
+
+def test_pair_report_arithmetic():
+    """The bench's per-pair figures from a step's counters (CPU, no GPU)."""
+    import bench as b
+    stats = {"rounds": 7, "scan_elements": 100, "s_cliques_listed": 50, "decrements": 20, "hash_probes": 0,
+             "link_calls": 10, "frontier_total": 40}
+    info = {(2, 3): {"n_r": 40, "n_s": 30, "n_nodes": 3, "stats": stats}}
+    rep = b.pair_report(info, {(2, 3): 2.0}, {(2, 3): 1.0}, {(2, 3): 5.0}, 1000.0)["2,3"]
+    alg = 4 * 100 + 4 * 2 * 50 + 8 * 20 + 8 * 10 + 12 * 40  # C(3,2) = 3 members, 2 others
+    assert b.algorithmic_peel_bytes(stats, 2, 3) == alg
+    assert rep["s_cliques_peeled_per_s"] == 30 / 0.002
+    assert abs(rep["peel_algorithmic_gbs"] - round(alg / 0.002 / 1e9, 3)) < 1e-12
+    assert rep["method"] == b.METHOD[(2, 3)]
+    assert rep["peel_frac_of_hbm_peak"] == (alg / 0.002 / 1e9) / 1000.0
