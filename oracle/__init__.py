@@ -192,6 +192,38 @@ def label_hierarchy(off, adj, r: int, s: int, labels) -> dict:
         lib.orc_free(p)
 
 
+def cut_hierarchy(leaf_node, node_parent, node_label, c: int) -> np.ndarray:
+    """The c-(r,s) nuclei read off a hierarchy (§8, dense subgraphs): remove every node of label
+    < c; each remaining subtree is one c-nucleus holding all its leaves.  Returns, per r-clique,
+    the id of the top node of its c-nucleus, or -1 when its smallest node has label < c (core < c)
+    or it has none."""
+    leaf_node = np.asarray(leaf_node)
+    node_parent = np.asarray(node_parent)
+    node_label = np.asarray(node_label)
+    top = {}
+
+    def top_of(N):
+        path = []
+        while N not in top:
+            path.append(N)
+            P = int(node_parent[N])
+            if P < 0 or node_label[P] < c:
+                top[N] = N
+                break
+            N = P
+        t = top[N]
+        for x in path:
+            top[x] = t
+        return t
+
+    out = np.full(len(leaf_node), -1, dtype=np.int64)
+    for R, N in enumerate(leaf_node):
+        N = int(N)
+        if N >= 0 and node_label[N] >= c:
+            out[R] = top_of(N)
+    return out
+
+
 def tree_from_uf(uf, L, core) -> dict:
     """construct-tree-efficient (Alg. 5) on given uf / L / core arrays."""
     lib = _load()

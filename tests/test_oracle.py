@@ -442,3 +442,61 @@ def test_label_hierarchy_singleton_waits_for_a_lower_level():
     res = oracle.label_hierarchy(off, adj, 1, 2, np.array([0, 3, 3, 5], dtype=np.uint32))
     assert tree_to_nodes(res["leaf_node"], res["node_parent"], res["node_label"]) == {frozenset({1, 2}): 3}
     assert res["leaf_node"][0] == -1 and res["leaf_node"][3] == -1
+
+
+# ---- c-(r,s) nuclei by cutting the hierarchy (§8, dense subgraph discovery) ----
+
+def _partition(labels):
+    groups = {}
+    for i, g in enumerate(labels):
+        if g >= 0:
+            groups.setdefault(int(g), set()).add(i)
+    return {frozenset(v) for v in groups.values()}
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (2, 3), (2, 4), (3, 4)])
+def test_cut_hierarchy_gives_the_c_nuclei(r, s):
+    """Cutting the tree at c equals the connected components, by definition, of the r-cliques of
+    core >= c joined through the s-cliques all of whose members have core >= c."""
+    rng = np.random.default_rng(300 + 10 * r + s)
+    checked = 0
+    for _ in range(25):
+        n = int(rng.integers(5, 11))
+        off, adj = gg.gnp(n, float(rng.uniform(0.4, 0.95)), int(rng.integers(1 << 30)))
+        o = oracle.nucleus(off, adj, r, s)
+        if o["n_r"] == 0:
+            continue
+        edges = _edges(off, adj)
+        b = brute_nucleus(n, edges, r, s)
+        for c in range(1, o["kmax"] + 1):
+            comp = oracle.cut_hierarchy(o["leaf_node"], o["node_parent"], o["node_label"], c)
+            # the components of X_c are the nodes of the brute-force hierarchy present at level c
+            want = {X for X, lab in b["nodes"].items() if lab >= c}
+            maximal = {X for X in want if not any(X < Y for Y in want)}
+            assert _partition(comp) == maximal
+            assert all((comp[R] >= 0) == (o["core"][R] >= c) for R in range(o["n_r"]))
+            checked += 1
+    assert checked > 20
+
+
+def test_cut_hierarchy_of_cliques_sharing_a_vertex():
+    """Two K5 sharing vertex 4 plus a separate K4.  (1,2): the K5 pair is one 4-nucleus (the
+    shared vertex connects them), the K4 a 3-nucleus.  (2,3): no triangle spans the two K5, so
+    at c = 3 they are two separate 3-nuclei of 10 edges each, and the K4's 6 edges a 2-nucleus."""
+    e = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    e += [(a, b) for a in range(4, 9) for b in range(a + 1, 9)]
+    e += [(a, b) for a in range(10, 14) for b in range(a + 1, 14)]
+    off, adj = gg.from_edges(14, sorted(set(e)))
+    o = oracle.nucleus(off, adj, 1, 2)
+    cut = lambda c: _partition(oracle.cut_hierarchy(o["leaf_node"], o["node_parent"], o["node_label"], c))
+    assert cut(4) == {frozenset(range(9))}
+    assert cut(3) == {frozenset(range(9)), frozenset(range(10, 14))}
+    assert cut(5) == set()
+    o = oracle.nucleus(off, adj, 2, 3)
+    tup = [tuple(t) for t in o["tuples"]]
+    edges_of = lambda vs: frozenset(i for i, (a, b) in enumerate(tup) if a in vs and b in vs)
+    A, B, K = edges_of(set(range(5))), edges_of(set(range(4, 9))), edges_of(set(range(10, 14)))
+    cut = lambda c: _partition(oracle.cut_hierarchy(o["leaf_node"], o["node_parent"], o["node_label"], c))
+    assert len(A) == len(B) == 10 and len(K) == 6
+    assert cut(3) == {A, B}
+    assert cut(2) == {A, B, K}
