@@ -118,3 +118,21 @@ def test_approx_bound_full_size(graph, gpu, r, s):
         assert (ap[nz] >= core[nz]).all()
         assert (ap[nz] <= (C + d) * (1 + d) * core[nz] + 1e-9).all()
         assert (ap <= g["cnt"]).all()
+
+
+@pytest.mark.parametrize("r,s", [(1, 2), (2, 3), (2, 4)])
+def test_two_phase_full_size(graph, gpu, r, s):
+    """The bench builds these pairs with the two-phase hierarchy (cores-only peel, then §7.4):
+    at full size its core numbers and round stamps equal the linking peel's, and its hierarchy
+    equals the linking peel's tree, which the tests above tie to the oracle."""
+    nc, o, ris = gpu
+    ri = ris[r]
+    cnt, _ = nc.count_s_cliques(o, ri, s)
+    el = nc.peel_and_link(o, ri, s, cnt)
+    p_el, l_el, nn_el = nc.construct_tree(el["core"], el["uf"], el["L"])
+    te = nc.peel_cores(o, ri, s, cnt)
+    assert torch.equal(te["core"], el["core"]) and torch.equal(te["round"], el["round"])
+    p_te, l_te, nn_te = nc.hierarchy_two_phase(o, ri, s, te["core"])
+    n_r = ri.n_r
+    p_el = p_el.cpu().numpy()
+    compare_hierarchy(p_te.cpu().numpy(), u32(l_te), nn_te, p_el[:n_r], p_el[n_r:n_r + nn_el], u32(l_el))
