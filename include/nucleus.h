@@ -61,6 +61,7 @@ typedef struct nh_peel_stats {
   uint64_t hash_probes;        /* r-clique hash look-ups (r = 3)                               */
   uint64_t frontier_total;     /* sum of frontier sizes                                        */
   uint64_t overflow_links;     /* link calls deferred to the device overflow queue             */
+  uint64_t stamp_reads;        /* round stamps (or core numbers) of members read while re-listing */
 } nh_peel_stats;
 
 /* a1 -- Arb-Orient (Alg. 3, first step; §3 on O(alpha)-orientations).
@@ -251,6 +252,25 @@ int nh_set_peel_max_group(int g);
  * s - r = 1, where one r-clique's link targets spread over many warps repeat walks.
  * n in [-1, 4096]; NH_ERR_INVALID otherwise.  Results never depend on it. */
 int nh_set_peel_task_items(int n);
+
+/* Tuning knob (process-wide, default 1): with on = 1 the (2,4) peel without links (link mode 2,
+ * the approximate peel) and the (2,4) two-phase / label hierarchies re-list each edge from its
+ * triangle list (built by nh_index_r_cliques for r = 2): candidates whose edges to the frontier
+ * edge were peeled earlier (or, in the hierarchy, lie below the level) are dropped before any
+ * pair is formed, the rest are staged in shared memory, and the decrements of one candidate's two
+ * edges are summed.  on = 0 uses the adjacency-scan re-listing of every other pair.  Results never
+ * depend on it.  NH_ERR_INVALID for other values. */
+int nh_set_peel_relist24(int on);
+
+/* Tuning knob of that (2,4) re-listing (process-wide): a frontier (or level) of at most 4096
+ * r-cliques is cut into sub-tasks, each staging its r-clique's whole candidate set and taking one
+ * share of its out-list scans; the sub-tasks of a round number about per_warp per warp of the
+ * grid, shared out by scan bound (list length plus the sum of the candidates' out-degrees), with
+ * a bound of at least warp_grain (block_grain for lists staged by a whole block) and at least
+ * len_mult times the list length per sub-task (0: no such floor).  Defaults (1, 128, 1024, 0).
+ * per_warp in [0.125, 64], warp_grain >= 32, block_grain >= 256, len_mult in [0, 1024];
+ * NH_ERR_INVALID otherwise.  Results never depend on it. */
+int nh_set_relist_split(float per_warp, int warp_grain, int block_grain, int len_mult);
 
 /* number of CUDA kernels this library has launched in the process so far (host counter) */
 int64_t nh_kernel_launches(void);

@@ -44,3 +44,14 @@ extern "C" int nh_debug_inject(int what, int64_t value) {
   }
   return NH_ERR_INVALID;
 }
+
+// round trace (include/nucleus_debug.h); read by the peel driver in nh_peel.cu
+uint64_t* g_nh_round_log = nullptr;
+long long g_nh_round_log_cap = 0;
+
+extern "C" int nh_debug_round_log(uint64_t* log, int64_t cap) {
+  if (cap < 0) return NH_ERR_INVALID;
+  g_nh_round_log = (cap > 0) ? log : nullptr;
+  g_nh_round_log_cap = (log != nullptr) ? (long long)cap : 0;
+  return NH_OK;
+}

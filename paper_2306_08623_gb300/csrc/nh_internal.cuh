@@ -14,6 +14,11 @@
 //                   so the key array of a few-million-edge graph stays resident in L2)
 //   etoff[m+1] (i64), etw[3 n_r], ettid[3 n_r]   r = 3: for every edge (p,q), the third vertices w
 //                   of all triangles {p,q,w} in ascending order, with the triangle ids
+//   t2off[m+1] (i64), t2w, t2ea, t2eb [3 T]   r = 2 (T = number of triangles): for every edge
+//                   (a,b), a < b, the third vertices w of its triangles in ascending order with the
+//                   ids of the edges {a,w} and {b,w} -- the s-cliques of (2,3) and the candidate sets
+//                   of (2,4) without any adjacency probe; t2cost[m] (u32, saturating): per edge the
+//                   sum over its list of the out-degrees d+(w), the (2,4) re-listing's work bound
 #pragma once
 
 #include <cuda_runtime.h>
@@ -60,6 +65,11 @@ struct nh_rindex {
   int64_t* etoff;
   int32_t* etw;
   int32_t* ettid;
+  int64_t* t2off;
+  int32_t* t2w;
+  int32_t* t2ea;
+  int32_t* t2eb;
+  uint32_t* t2cost;
   cudaStream_t stream;
 };
 
@@ -83,6 +93,11 @@ struct GView {
   const int64_t* etoff;
   const int32_t* etw;
   const int32_t* ettid;
+  const int64_t* t2off;
+  const int32_t* t2w;
+  const int32_t* t2ea;
+  const int32_t* t2eb;
+  const uint32_t* t2cost;
   int64_t n, m;
 };
 
@@ -98,6 +113,11 @@ static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
   g.etoff = ri ? ri->etoff : nullptr;
   g.etw = ri ? ri->etw : nullptr;
   g.ettid = ri ? ri->ettid : nullptr;
+  g.t2off = ri ? ri->t2off : nullptr;
+  g.t2w = ri ? ri->t2w : nullptr;
+  g.t2ea = ri ? ri->t2ea : nullptr;
+  g.t2eb = ri ? ri->t2eb : nullptr;
+  g.t2cost = ri ? ri->t2cost : nullptr;
   g.n = o->n; g.m = o->m;
   return g;
 }

@@ -243,6 +243,62 @@ __global__ void k_et_fill(int64_t m, const int64_t* __restrict__ off, const int3
   }
 }
 
+// r = 2: per edge (a,b), the third vertices w of its triangles in ascending order with the ids of
+// the edges {a,w} and {b,w} (read from the adjacency positions of the intersection, no probe)
+__global__ void k_et2_fill(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ eid, const int32_t* __restrict__ eu,
+                           const int32_t* __restrict__ ev, const int64_t* __restrict__ t2off,
+                           int32_t* __restrict__ t2w, int32_t* __restrict__ t2ea, int32_t* __restrict__ t2eb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int32_t a = eu[e], b = ev[e];
+    int64_t sb = off[a], se = off[a + 1], lb = off[b], le = off[b + 1];
+    const bool scan_a = (se - sb) <= (le - lb);
+    if (!scan_a) {
+      int64_t t0 = sb, t1 = se;
+      sb = lb; se = le; lb = t0; le = t1;
+    }
+    int64_t pos = t2off[e];
+    for (int64_t base = sb; base < se; base += 32) {
+      const int64_t j = base + lane;
+      int32_t w = 0;
+      int64_t q = -1;
+      if (j < se) {
+        w = adj[j];
+        q = nh_find(adj, lb, le, w);
+      }
+      const unsigned msk = __ballot_sync(NH_FULL, q >= 0);
+      if (q >= 0) {
+        const int64_t k = pos + __popc(msk & ((1u << lane) - 1u));
+        t2w[k] = w;
+        t2ea[k] = eid[scan_a ? j : q];
+        t2eb[k] = eid[scan_a ? q : j];
+      }
+      pos += __popc(msk);
+    }
+  }
+}
+
+// per edge: the sum of d+(w) over its triangle list (saturating at 2^32 - 1)
+__global__ void k_et2_cost(int64_t m, const int64_t* __restrict__ ooff, const int64_t* __restrict__ t2off,
+                           const int32_t* __restrict__ t2w, uint32_t* __restrict__ t2cost) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    unsigned long long sum = 0;
+    for (int64_t j = t2off[e] + lane; j < t2off[e + 1]; j += 32) {
+      const int32_t w = t2w[j];
+      sum += (unsigned long long)(ooff[w + 1] - ooff[w]);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(NH_FULL, sum, d);
+    if (lane == 0) t2cost[e] = sum > 0xffffffffull ? 0xffffffffu : (uint32_t)sum;
+  }
+}
+
 __global__ void k_edge_insert(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                               unsigned long long* __restrict__ ekey, uint32_t* __restrict__ eval,
                               unsigned long long mask, int* __restrict__ status) {
@@ -305,6 +361,7 @@ void free_rindex(nh_rindex* ri) {
   if (!ri) return;
   cudaFree(ri->tri); cudaFree(ri->toff); cudaFree(ri->table);
   cudaFree(ri->etoff); cudaFree(ri->etw); cudaFree(ri->ettid);
+  cudaFree(ri->t2off); cudaFree(ri->t2w); cudaFree(ri->t2ea); cudaFree(ri->t2eb); cudaFree(ri->t2cost);
   delete ri;
 }
 
@@ -432,7 +489,51 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
   nh_rindex* ri = new nh_rindex();
   ri->r = r; ri->o = o; ri->stream = st;
   if (r == 1) ri->n_r = o->n;
-  if (r == 2) ri->n_r = o->m;
+  if (r == 2) {
+    ri->n_r = o->m;
+    // per-edge triangle lists with the ids of the two other edges: the (2,3) s-cliques and the
+    // (2,4) candidate sets of every edge.  Optional: without device memory for them (36 bytes per
+    // triangle) the peels fall back to adjacency scans with edge-table probes.
+    const int64_t m = o->m;
+    if (m > 0) {
+      uint32_t* tcount = nullptr;
+      int rc = nh_alloc(&tcount, m, st);
+      if (!rc) rc = nh_alloc(&ri->t2off, m + 1, st);
+      if (!rc) {
+        k_et_count<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eu, o->ev, tcount);
+        nh_note_launch();
+        rc = nh_exclusive_scan_u32(tcount, ri->t2off, m, st);
+      }
+      int64_t tot = 0;
+      if (!rc) {
+        cudaMemcpyAsync(&tot, ri->t2off + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = NH_ERR_CUDA;
+      }
+      nh_free(tcount, st);
+      if (!rc && tot >= (1ll << 31)) rc = NH_ERR_UNSUPPORTED;  // positions are int32 in the peel
+      if (!rc) rc = nh_alloc(&ri->t2w, tot, st);
+      if (!rc) rc = nh_alloc(&ri->t2ea, tot, st);
+      if (!rc) rc = nh_alloc(&ri->t2eb, tot, st);
+      if (!rc) rc = nh_alloc(&ri->t2cost, m, st);
+      if (!rc) {
+        k_et2_fill<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eid, o->eu, o->ev, ri->t2off, ri->t2w,
+                                                       ri->t2ea, ri->t2eb);
+        k_et2_cost<<<warp_grid(m), kThreads, 0, st>>>(m, o->ooff, ri->t2off, ri->t2w, ri->t2cost);
+        nh_note_launch(2);
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+      }
+      if (rc == NH_ERR_CUDA) {
+        free_rindex(ri);
+        return rc;
+      }
+      if (rc) {  // no room (or too many triangles): run without the lists
+        (void)cudaGetLastError();
+        cudaFree(ri->t2off); cudaFree(ri->t2w); cudaFree(ri->t2ea); cudaFree(ri->t2eb); cudaFree(ri->t2cost);
+        ri->t2off = nullptr; ri->t2w = ri->t2ea = ri->t2eb = nullptr;
+        ri->t2cost = nullptr;
+      }
+    }
+  }
   if (r == 3) {
     const int64_t m = o->m;
     uint32_t* tcount = nullptr;

@@ -26,8 +26,13 @@
 #include "nh_peel.cuh"
 
 extern long long g_nh_inject_wait_ns;  // fault injection (nh_api.cu): grid-barrier wait limit
+extern uint64_t* g_nh_round_log;       // round trace (nh_api.cu)
+extern long long g_nh_round_log_cap;
 static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
 static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
+static int g_peel_relist24 = 1;       // set by nh_set_peel_relist24
+static float g_split_per_warp = 1.0f;  // set by nh_set_relist_split
+static int g_split_wgrain = 128, g_split_bgrain = 1024, g_split_len_mult = 0;
 
 namespace nhp {
 
@@ -120,7 +125,8 @@ int two_phase_launch_pair(int r, int s, PeelArgs& A, TreeOut& T, cudaStream_t st
 // chunk counts of the re-listed lists (they depend on r, and for r = 3 on s)
 int chunk_cost_pair(int r, int s, const GView& g, int64_t n_r, uint32_t* cost, cudaStream_t st) {
   if (r == 1) return chunk_cost_12(g, n_r, cost, st);
-  if (r == 2) return chunk_cost_23(g, n_r, cost, st);
+  if (r == 2 && s == 3) return chunk_cost_23(g, n_r, cost, st);
+  if (r == 2 && s == 4) return chunk_cost_24(g, n_r, cost, st);
   if (r == 3 && s == 4) return chunk_cost_34(g, n_r, cost, st);
   return NH_ERR_UNSUPPORTED;
 }
@@ -163,6 +169,13 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   A.lk.L = L;
   A.lk.core = val;
   A.lk.ovf_cap = (unsigned long long)(n_r / 4 > (1 << 20) ? n_r / 4 : (1 << 20));
+  A.use24 = (r == 2 && s == 4 && ri->t2off && g_peel_relist24 && (!exact || link_mode == 2)) ? 1 : 0;
+  A.c24_per_warp = g_split_per_warp;
+  A.c24_wgrain = g_split_wgrain;
+  A.c24_bgrain = g_split_bgrain;
+  A.c24_len_mult = g_split_len_mult;
+  A.round_log = reinterpret_cast<unsigned long long*>(g_nh_round_log);
+  A.round_log_cap = (unsigned long long)g_nh_round_log_cap;
   int rc = NH_OK;
   uint32_t* thr_dev = nullptr;
   unsigned int* dmax = nullptr;
@@ -173,6 +186,11 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
       (rc = nh_alloc(&A.front[1], n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) ||
       (rc = nh_alloc(&cost, n_r, st))) {
     goto cleanup;
+  }
+  if (A.use24) {
+    A.c24_qcap = (unsigned long long)(n_r + kC24QueueSlack);
+    if ((rc = nh_alloc(&A.c24_queue, (int64_t)A.c24_qcap, st))) goto cleanup;
+    cudaMemsetAsync(A.c24_queue, 0xff, sizeof(unsigned long long) * A.c24_qcap, st);
   }
   if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
@@ -242,13 +260,14 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
       stats->hash_probes = h.st_probe;
       stats->frontier_total = h.st_front;
       stats->overflow_links = h.st_ovf;
+      stats->stamp_reads = h.st_stamp;
     }
   }
 cleanup:
   nh_free(A.cnt, st); nh_free(A.alive[0], st); nh_free(A.alive[1], st); nh_free(A.front[0], st);
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
   nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
-  nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st);
+  nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st); nh_free(A.c24_queue, st);
   if (res_dev) return (cudaGetLastError() != cudaSuccess && !rc) ? NH_ERR_CUDA : rc;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
@@ -392,6 +411,11 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   A.stats = 0;
   A.timeout_ns = g_nh_inject_wait_ns > 0 ? (unsigned long long)g_nh_inject_wait_ns : 60ull * 1000000000ull;
   A.touched_cap = 2ull * (unsigned long long)n_r + 64;
+  A.use24 = (r == 2 && s == 4 && ri->t2off && g_peel_relist24) ? 1 : 0;
+  A.c24_per_warp = g_split_per_warp;
+  A.c24_wgrain = g_split_wgrain;
+  A.c24_bgrain = g_split_bgrain;
+  A.c24_len_mult = g_split_len_mult;
   unsigned int* dmax = nullptr;
   uint32_t* hist = nullptr;
   int64_t* off = nullptr;
@@ -409,8 +433,11 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   if ((rc = nh_alloc(&A.lk.uf, n_r, st)) || (rc = nh_alloc(&A.lk.ctl, 1, st)) || (rc = nh_alloc(&A.touched, (int64_t)A.touched_cap, st)) ||
       (rc = nh_alloc(&A.touched_n, 1, st)) || (rc = nh_alloc(&T.lvl, n_r, st)) || (rc = nh_alloc(&T.nid, n_r, st)) ||
       (rc = nh_alloc(&T.top, n_r, st)) || (rc = nh_alloc(&T.node_count, 1, st)) || (rc = nh_alloc(&dmax, 1, st)) ||
-      (rc = nh_alloc(&order, n_r, st)) || (rc = nh_alloc(&cost, n_r, st)))
+      (rc = nh_alloc(&order, n_r, st)) || (rc = nh_alloc(&cost, n_r, st)) ||
+      (A.use24 && (rc = nh_alloc(&A.c24_queue, n_r + kC24QueueSlack, st))))
     goto cleanup;
+  A.c24_qcap = (unsigned long long)(n_r + kC24QueueSlack);
+  if (A.use24) cudaMemsetAsync(A.c24_queue, 0xff, sizeof(unsigned long long) * A.c24_qcap, st);
   if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
   cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
@@ -454,7 +481,7 @@ cleanup:
   nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
   nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
   nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(cost, st);
-  nh_free(mark, st);
+  nh_free(mark, st); nh_free(A.c24_queue, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }
@@ -472,6 +499,23 @@ extern "C" int nh_label_hierarchy(const nh_oriented* o, const nh_rindex* ri, int
 extern "C" int nh_set_peel_max_group(int g) {
   if (g < 1 || g > 1024 || (g & (g - 1))) return NH_ERR_INVALID;
   g_peel_max_group = g;
+  return NH_OK;
+}
+
+extern "C" int nh_set_peel_relist24(int on) {
+  if (on != 0 && on != 1) return NH_ERR_INVALID;
+  g_peel_relist24 = on;
+  return NH_OK;
+}
+
+extern "C" int nh_set_relist_split(float per_warp, int warp_grain, int block_grain, int len_mult) {
+  if (!(per_warp >= 0.125f && per_warp <= 64.0f) || warp_grain < 32 || block_grain < 256 || len_mult < 0 ||
+      len_mult > 1024)
+    return NH_ERR_INVALID;
+  g_split_per_warp = per_warp;
+  g_split_wgrain = warp_grain;
+  g_split_bgrain = block_grain;
+  g_split_len_mult = len_mult;
   return NH_OK;
 }
 

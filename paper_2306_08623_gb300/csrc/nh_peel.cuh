@@ -13,6 +13,7 @@ constexpr int kThreads = 256;
 constexpr int kTaskItems = 4096;  // largest frontier re-listed in work-proportional tasks
 constexpr int kMinBlocks = 4;     // resident blocks per SM the persistent kernels are compiled for
 constexpr int kLinkStack = 16;
+constexpr int64_t kC24QueueSlack = 1 << 16;  // block sub-tasks of a round beyond one per r-clique
 constexpr uint32_t kNone = 0xffffffffu;
 
 struct PeelCtl {
@@ -41,9 +42,14 @@ struct PeelCtl {
   unsigned long long drain_n;
   unsigned long long ovf_count[2];
   unsigned long long task_next;     // next re-listing task of the round (work-proportional mode)
+  unsigned long long c24_next;      // (2,4) triangle-list re-listing: next list item for warps,
+  unsigned long long c24_hn;        // entries pushed to the block queue,
+  unsigned long long c24_hk;        // entries taken from it
+  unsigned long long c24_tasks;     // sub-tasks of the round (round trace)
+  unsigned long long dbg_work;      // list entries expanded in the round (round trace)
   // statistics
   unsigned long long st_rounds, st_levels, st_listed, st_dec, st_link, st_unite, st_scan, st_probe, st_front,
-      st_ovf;
+      st_ovf, st_stamp;
 };
 
 struct LinkEnv {
@@ -81,11 +87,19 @@ struct PeelArgs {
   unsigned long long touched_cap;
   int stats;
   unsigned long long timeout_ns;
+  int use24;              // (2,4) without links: re-list over the per-edge triangle lists
+  unsigned long long* round_log;  // optional trace: per round (frontier << 32 | levels, end time)
+  unsigned long long round_log_cap;
+  unsigned long long* c24_queue;  // block queue of that re-listing (all ~0 between rounds)
+  unsigned long long c24_qcap;    // its entries: n_r + kC24QueueSlack (sub-tasks of a round)
+  float c24_per_warp;             // sub-tasks per warp of the grid a round aims at
+  int c24_wgrain, c24_bgrain;     // least scan bound per warp / block sub-task
+  int c24_len_mult;               // and at least this many times the list length (0: off)
   LinkEnv lk;
 };
 
 struct LocalStats {
-  unsigned long long listed, dec, link, unite, scan, probe, ovf;
+  unsigned long long listed, dec, link, unite, scan, probe, ovf, stamp;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -320,7 +334,7 @@ __device__ __forceinline__ void add_delta(LocalStats& ls, const LinkDelta& d) {
 }
 
 static __device__ __noinline__ LinkDelta link_run_call(const LinkEnv E, int32_t R0, int32_t Q0) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
   link_run(E, R0, Q0, ls);
   return LinkDelta{ls.link, ls.unite, ls.ovf};
 }
@@ -371,6 +385,15 @@ struct WarpLinks {
 
 constexpr int kSeen = 64;
 
+// dynamic shared memory of the persistent kernels on the adjacency / chunk-task path: per warp a
+// link buffer and a seen-roots filter, the task prefix sums, per-warp sums, per-warp buffer counts
+constexpr int kSmLinks = 0;
+constexpr int kSmPref = kSmLinks + (kThreads / 32) * kLinkBuf * 8;
+constexpr int kSmSeen = kSmPref + kTaskItems * 4;
+constexpr int kSmWsum = kSmSeen + (kThreads / 32) * kSeen * 4;
+constexpr int kSmLcnt = kSmWsum + (kThreads / 32) * 8;
+constexpr int kSmOldBytes = kSmLcnt + (kThreads / 32) * 4;
+
 // warp-collective: forget the roots seen for the previous frontier r-clique
 __device__ __forceinline__ void wl_begin(const WarpLinks& W, int lane) {
   __syncwarp();
@@ -394,7 +417,7 @@ __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, in
 // registers
 static __device__ __noinline__ LinkDelta wl_flush_impl(const WarpLinks W, const LinkEnv E, const uint32_t* val,
                                                        int32_t Rid, int lane) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
   __syncwarp();
   const int n = min(*(volatile int*)W.cnt, kLinkBuf);
   if (n == 0) return LinkDelta{0, 0, 0};
@@ -530,12 +553,14 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 // ---------------------------------------------------------------------------------------------
 
 // Length of the list whose 32-entry chunks the re-listing of r-clique Rid walks: the adjacency
-// list of its vertex of least degree, or for (3,4) the shortest triangle list of its three edges.
+// list of its vertex of least degree, for (2,3) with per-edge triangle lists the edge's own list,
+// or for (3,4) the shortest triangle list of its three edges.
 template <int R, int S>
 __device__ __forceinline__ int64_t relist_len(const GView& g, int32_t Rid) {
   if constexpr (R == 1) {
     return __ldg(g.off + Rid + 1) - __ldg(g.off + Rid);
   } else if constexpr (R == 2) {
+    if (S == 3 && g.t2off) return __ldg(g.t2off + Rid + 1) - __ldg(g.t2off + Rid);
     const int32_t u = __ldg(g.eu + Rid), v = __ldg(g.ev + Rid);
     const int64_t du = __ldg(g.off + u + 1) - __ldg(g.off + u), dv = __ldg(g.off + v + 1) - __ldg(g.off + v);
     return du < dv ? du : dv;
@@ -639,6 +664,22 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
       if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
     }
     return;
+  }
+  if constexpr (R == 2 && S == 3) {
+    if (g.t2off) {
+      // the triangles of edge Rid are its triangle list: members {a,w} and {b,w} read directly
+      const int64_t b0 = __ldg(g.t2off + Rid), b1 = __ldg(g.t2off + Rid + 1);
+      if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(2 * (b1 - b0));
+      for (int64_t c = c0; c < cend && b0 + 32 * c < b1; c += cstep) {
+        const int64_t j = b0 + 32 * c + lane;
+        if (j < b1) {
+          const int32_t mem[2] = {__ldg(g.t2ea + j), __ldg(g.t2eb + j)};
+          process_S<2, EXACT>(A, Rid, mem, t, thr, nf, W, ls);
+        }
+        if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
+      }
+      return;
+    }
   }
   int64_t lo[3], hi[3];
 #pragma unroll
@@ -865,6 +906,12 @@ __device__ __forceinline__ void relist_list(const PeelArgs& A, const int32_t* it
   }
 }
 
+}  // namespace nhp
+
+#include "nh_relist24.cuh"
+
+namespace nhp {
+
 // ---------------------------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------------------------
@@ -894,6 +941,9 @@ template <bool EXACT>
 __device__ void leader_end_of_round(const PeelArgs& A) {
   PeelCtl* c = A.lk.ctl;
   c->task_next = 0;
+  c->c24_next = 0;
+  c->c24_hn = 0;
+  c->c24_hk = 0;
   const unsigned int oc = c->ovf_cur;
   if (c->ovf_count[oc] > 0) {
     c->draining = 1;
@@ -905,6 +955,14 @@ __device__ void leader_end_of_round(const PeelArgs& A) {
   }
   c->draining = 0;
   c->finished += c->fsize;
+  if (A.round_log && c->st_rounds < A.round_log_cap) {
+    unsigned long long* L = A.round_log + 4 * c->st_rounds;
+    L[0] = (c->fsize << 32) | (c->st_levels & 0xffffffffull);
+    L[1] = nh_globaltimer();
+    L[2] = c->dbg_work;
+    L[3] = (c->c24_tasks << 32) | (c->c24_hn & 0xffffffffull);
+    c->dbg_work = 0;
+  }
   c->st_rounds++;
   c->st_front += c->fsize;
   if (c->thr > c->kmax && c->fsize > 0) c->kmax = c->thr;
@@ -933,22 +991,29 @@ __device__ void leader_end_of_round(const PeelArgs& A) {
   }
 }
 
+// resident blocks per SM a kernel is compiled for: (2,4) stages candidates in about 50 KB of
+// shared memory per block and gets the registers of three blocks per SM
+template <int R, int S>
+constexpr int min_blocks() { return (R == 2 && S == 4) ? 3 : kMinBlocks; }
+
 template <int R, int S, bool EXACT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_peel(PeelArgs A) {
+__global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs A) {
   PeelCtl* ctl = A.lk.ctl;
   volatile PeelCtl* vc = ctl;
   const int lane = threadIdx.x & 31;
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
-  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
-  __shared__ int s_lcnt[kThreads / 32];
-  __shared__ int32_t s_seen[kThreads / 32][kSeen];
-  __shared__ uint32_t s_pref[kTaskItems];
-  __shared__ unsigned long long s_wsum[kThreads / 32];
-  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  unsigned long long* s_links = reinterpret_cast<unsigned long long*>(s_dyn + kSmLinks);
+  uint32_t* s_pref = reinterpret_cast<uint32_t*>(s_dyn + kSmPref);
+  int32_t* s_seen = reinterpret_cast<int32_t*>(s_dyn + kSmSeen);
+  unsigned long long* s_wsum = reinterpret_cast<unsigned long long*>(s_dyn + kSmWsum);
+  int* s_lcnt = reinterpret_cast<int*>(s_dyn + kSmLcnt);
+  const bool use24 = (R == 2 && S == 4) && A.use24;
+  if (!use24 && lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
-  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
+  const WarpLinks W{s_links + (threadIdx.x >> 5) * kLinkBuf, &s_lcnt[threadIdx.x >> 5], s_seen + (threadIdx.x >> 5) * kSeen};
   for (;;) {
     if (vc->done || vc->err) break;
     if (vc->need_scan) {
@@ -1013,11 +1078,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_peel(PeelArgs A) {
       const unsigned long long fs = vc->fsize;
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
-      unsigned long long total = 0;
-      const bool tasks = fs <= (unsigned long long)A.task_items &&
-                         relist_prefix<R, S>(A, fr, (unsigned int)fs, lane, s_pref, s_wsum, total);
-      relist_list<R, S, EXACT>(A, fr, fs, tasks, total, t, thr, nf, lane, gwarp, nwarps, W, ls, s_pref,
-                               &ctl->task_next);
+      if (use24) {
+        c24_list<EXACT>(A, fr, fs, t, thr, nf, nwarps, s_dyn, ls);
+      } else {
+        unsigned long long total = 0;
+        const bool tasks = fs <= (unsigned long long)A.task_items &&
+                           relist_prefix<R, S>(A, fr, (unsigned int)fs, lane, s_pref, s_wsum, total);
+        relist_list<R, S, EXACT>(A, fr, fs, tasks, total, t, thr, nf, lane, gwarp, nwarps, W, ls, s_pref,
+                                 &ctl->task_next);
+      }
     }
     // end of round: drain deferred link calls, then advance
     bool ok = true;
@@ -1037,8 +1106,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_peel(PeelArgs A) {
   if (A.stats) {
     const unsigned long long v0 = warp_sum_u64(ls.listed), v1 = warp_sum_u64(ls.dec), v2 = warp_sum_u64(ls.link),
                              v3 = warp_sum_u64(ls.unite), v4 = warp_sum_u64(ls.scan), v5 = warp_sum_u64(ls.probe),
-                             v6 = warp_sum_u64(ls.ovf);
+                             v6 = warp_sum_u64(ls.ovf), v7 = warp_sum_u64(ls.stamp);
     if (lane == 0) {
+      atomicAdd(&ctl->st_stamp, v7);
       atomicAdd(&ctl->st_listed, v0);
       atomicAdd(&ctl->st_dec, v1);
       atomicAdd(&ctl->st_link, v2);
@@ -1058,11 +1128,13 @@ int launch_peel(PeelArgs& A, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return NH_ERR_UNSUPPORTED;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1)
+  const int smem = A.use24 ? kC24SmemBytes : kSmOldBytes;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return NH_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess || per < 1)
     return NH_ERR_CUDA;
   dim3 grid((unsigned)(sms * per)), block(kThreads);
   void* args[] = {&A};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, st);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, block, args, (size_t)smem, st);
   nh_note_launch();
   return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }
@@ -1090,7 +1162,7 @@ struct TreeOut {
 };
 
 template <int R, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_two_phase(PeelArgs A, TreeOut T) {
+__global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(PeelArgs A, TreeOut T) {
   PeelCtl* ctl = A.lk.ctl;
   volatile PeelCtl* vc = ctl;
   const int lane = threadIdx.x & 31;
@@ -1098,27 +1170,39 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_two_phase(PeelArgs A, 
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
-  __shared__ unsigned long long s_links[kThreads / 32][kLinkBuf];
-  __shared__ int s_lcnt[kThreads / 32];
-  __shared__ int32_t s_seen[kThreads / 32][kSeen];
-  __shared__ uint32_t s_pref[kTaskItems];
-  __shared__ unsigned long long s_wsum[kThreads / 32];
-  if (lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  unsigned long long* s_links = reinterpret_cast<unsigned long long*>(s_dyn + kSmLinks);
+  uint32_t* s_pref = reinterpret_cast<uint32_t*>(s_dyn + kSmPref);
+  int32_t* s_seen = reinterpret_cast<int32_t*>(s_dyn + kSmSeen);
+  unsigned long long* s_wsum = reinterpret_cast<unsigned long long*>(s_dyn + kSmWsum);
+  int* s_lcnt = reinterpret_cast<int*>(s_dyn + kSmLcnt);
+  const bool use24 = (R == 2 && S == 4) && A.use24;
+  if (!use24 && lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
-  const WarpLinks W{s_links[threadIdx.x >> 5], &s_lcnt[threadIdx.x >> 5], s_seen[threadIdx.x >> 5]};
+  const WarpLinks W{s_links + (threadIdx.x >> 5) * kLinkBuf, &s_lcnt[threadIdx.x >> 5], s_seen + (threadIdx.x >> 5) * kSeen};
   const int64_t n_r = A.n_r;
   for (uint32_t level = T.kmax; level >= 1; --level) {
     const int64_t lo = T.lvl_off[level], hi = T.lvl_off[level + 1];
     const unsigned long long cnt = (unsigned long long)(hi - lo);
     if (cnt == 0) continue;
     // unions at this level
-    unsigned long long total = 0;
-    const bool tasks = cnt <= (unsigned long long)A.task_items &&
-                       relist_prefix<R, S>(A, T.order + lo, (unsigned int)cnt, lane, s_pref, s_wsum, total);
-    relist_list<R, S, true>(A, T.order + lo, cnt, tasks, total, 0u, level, nullptr, lane, gwarp, nwarps, W, ls,
-                            s_pref, &ctl->task_next);
-    if (!grid_sync(ctl, A.timeout_ns, [&] { ctl->task_next = 0; })) break;
+    if (use24) {
+      c24_list<true>(A, T.order + lo, cnt, 0u, level, nullptr, nwarps, s_dyn, ls);
+    } else {
+      unsigned long long total = 0;
+      const bool tasks = cnt <= (unsigned long long)A.task_items &&
+                         relist_prefix<R, S>(A, T.order + lo, (unsigned int)cnt, lane, s_pref, s_wsum, total);
+      relist_list<R, S, true>(A, T.order + lo, cnt, tasks, total, 0u, level, nullptr, lane, gwarp, nwarps, W, ls,
+                              s_pref, &ctl->task_next);
+    }
+    if (!grid_sync(ctl, A.timeout_ns, [&] {
+          ctl->task_next = 0;
+          ctl->c24_next = 0;
+          ctl->c24_hn = 0;
+          ctl->c24_hk = 0;
+        }))
+      break;
     // a node for every component holding an r-clique of this level (with labels that are not
     // core numbers, an r-clique in no s-clique at its own level is alone there: no node; it
     // becomes a leaf of the first node its component gets at a lower level, through the touched
@@ -1180,9 +1264,11 @@ int launch_two_phase(PeelArgs& A, TreeOut& T, cudaStream_t st) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, 0) != cudaSuccess || per < 1) return NH_ERR_CUDA;
+  const int smem = A.use24 ? kC24SmemBytes : kSmOldBytes;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return NH_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess || per < 1) return NH_ERR_CUDA;
   void* args[] = {&A, &T};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(sms * per)), dim3(kThreads), args, 0, st);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(sms * per)), dim3(kThreads), args, (size_t)smem, st);
   nh_note_launch();
   return e == cudaSuccess ? NH_OK : NH_ERR_CUDA;
 }

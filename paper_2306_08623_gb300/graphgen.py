@@ -156,6 +156,34 @@ def chung_lu(n: int, beta: float, mean_deg: float, seed: int, groups: int = 0, p
     return csr_from_pairs(n, u, v)
 
 
+def shared_hubs(commons, inner_deg: float, seed: int, extra: int = 0):
+    """Adjacent hub pairs with long shared neighbourhoods: for each k in ``commons`` two new hub
+    vertices, joined to each other and to the same k fresh vertices, whose k vertices get about
+    k * inner_deg / 2 random edges among themselves; the hub edge then lies in k triangles and
+    in one 4-clique per inner edge.  ``extra`` random vertices with the same inner density are
+    attached to random shared vertices.  Exercises long per-edge triangle lists."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    us, vs = [], []
+    base = 0
+    for k in commons:
+        a, b = base, base + 1
+        W = np.arange(base + 2, base + 2 + k, dtype=np.int64)
+        us += [np.array([a]), np.full(k, a), np.full(k, b)]
+        vs += [np.array([b]), W, W]
+        E = int(k * inner_deg / 2)
+        us.append(rng.choice(W, size=E))
+        vs.append(rng.choice(W, size=E))
+        base += 2 + k
+    n = base + extra
+    if extra and base > 0:
+        X = np.arange(base, n, dtype=np.int64)
+        us.append(np.repeat(X, 3))
+        vs.append(rng.integers(0, base, size=3 * extra))
+    if not us:
+        return csr_from_pairs(max(n, 1), [], [])
+    return csr_from_pairs(n, np.concatenate(us), np.concatenate(vs))
+
+
 def batch_member(seed: int):
     """One graph of the 512-graph batch: n log-uniform in [1e3, 2e5], mean degree U[8, 40],
     family by seed mod 3: Erdos-Renyi, R-MAT (scale ceil(log2 n), ids >= n dropped), Chung-Lu

@@ -30,6 +30,7 @@ class PeelStats(ctypes.Structure):
         ("reserved", ctypes.c_uint32), ("s_cliques_listed", ctypes.c_uint64), ("decrements", ctypes.c_uint64),
         ("link_calls", ctypes.c_uint64), ("unites", ctypes.c_uint64), ("scan_elements", ctypes.c_uint64),
         ("hash_probes", ctypes.c_uint64), ("frontier_total", ctypes.c_uint64), ("overflow_links", ctypes.c_uint64),
+        ("stamp_reads", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -65,6 +66,9 @@ def lib():
             "nh_label_hierarchy": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), P]),
             "nh_set_peel_max_group": (I32, [I32]),
             "nh_set_peel_task_items": (I32, [I32]),
+            "nh_set_peel_relist24": (I32, [I32]),
+            "nh_set_relist_split": (I32, [ctypes.c_float, I32, I32, I32]),
+            "nh_debug_round_log": (I32, [P, I64]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
             "nh_link_pairs": (I32, [I64, P, P, P, P, I64, P]),
             "nh_status_string": (ctypes.c_char_p, [I32]),
@@ -381,6 +385,34 @@ def set_peel_task_items(n: int):
     """Largest frontier (or level) re-listed as work-proportional chunk tasks (0..4096, 0 = off,
     -1 = automatic); results never depend on it."""
     _check("nh_set_peel_task_items", lib().nh_set_peel_task_items(int(n)))
+
+
+def set_peel_relist24(on: bool):
+    """(2,4) without links: re-list each edge from its triangle list with candidates staged in
+    shared memory (True, the default) or by the adjacency scans of the other pairs (False);
+    results never depend on it."""
+    _check("nh_set_peel_relist24", lib().nh_set_peel_relist24(int(bool(on))))
+
+
+RELIST_SPLIT_DEFAULT = (1.0, 128, 1024, 0)
+
+
+def set_relist_split(per_warp: float = 1.0, warp_grain: int = 128, block_grain: int = 1024, len_mult: int = 0):
+    """Sub-task split of the (2,4) triangle-list re-listing (see nucleus.h); results never depend
+    on it."""
+    _check("nh_set_relist_split", lib().nh_set_relist_split(float(per_warp), int(warp_grain), int(block_grain),
+                                                            int(len_mult)))
+
+
+def debug_round_log(log: torch.Tensor | None):
+    """Trace the rounds of the next peels into log (int64 device tensor of 4*cap entries): per
+    round (frontier size << 32 | levels opened so far, device timer in ns at the round's end,
+    out-list entries expanded, sub-tasks << 32 | block sub-tasks); None turns the trace off."""
+    if log is None:
+        _check("nh_debug_round_log", lib().nh_debug_round_log(None, 0))
+    else:
+        assert log.dtype == torch.int64 and log.is_cuda
+        _check("nh_debug_round_log", lib().nh_debug_round_log(_dptr(log), log.numel() // 4))
 
 
 def _cuda_timer(run) -> float:
