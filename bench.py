@@ -3,20 +3,24 @@
 
 Workload (one step): the (1,2), (2,3), (2,4) and (3,4) exact hierarchies of the R-MAT graph with
 scale 18, edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05), seed 2 (symmetrised, de-duplicated;
-3.81M edges, 82.7M triangles): orientation, r-clique index (r = 1,2,3), s-clique counts, peel with
-link-efficient and construct-tree for every pair.  value = s-cliques peeled per second of step
-time (sum of n_s over the four pairs / step time).
+3.81M edges, 82.7M triangles): orientation, r-clique index (r = 1,2,3), s-clique counts, peel and
+hierarchy for every pair.  value = s-cliques peeled per second of step time (sum of n_s over the
+four pairs / step time).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
 
 N > 1 runs N independent replicas (torchrun, one rank per GPU; the peel does not shard), value =
 all ranks' s-cliques / max-over-ranks time.  --impl reference times the sequential CPU oracle on
-a bounded sample of the same workload on the host cores.
+a bounded sample of the same workload on the host cores.  Beside the headline step the default
+run also measures, once each and in the same JSON line: the learned vs degree work partition on
+the Chung-Lu graph (n = 4M), the 512-graph batch (batched vs one by one), and the approximate
+peel on R-MAT 22 (2,3) / R-MAT 20 (3,4) beside the exact one.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -32,12 +36,12 @@ UNIT = "s-cliques/s"
 PAIRS = [(1, 2), (2, 3), (2, 4), (3, 4)]
 # hierarchy builder per pair: link-efficient interleaved with the peel (anh-el, Alg. 3 + Alg. 5)
 # or the two-phase hierarchy from final core numbers (anh-te, §7.4), whichever builds this graph's
-# hierarchy faster on a GB300 (R-MAT 18, ms of peel + hierarchy, el / te: (1,2) 39 / 21,
-# (2,3) 187 / 165, (2,4) 28000 / 8700, (3,4) 2335 / 2608); the other one is timed beside the step
+# hierarchy faster on a GB300 (the other one is timed beside the step)
 METHOD = {(1, 2): "te", (2, 3): "te", (2, 4): "te", (3, 4): "el"}
 WORKLOAD = ("RMAT scale 18 EF16 (0.57,0.19,0.19,0.05) seed 2; exact (1,2),(2,3),(2,4),(3,4) hierarchies "
             "(anh-el for (3,4), anh-te for the others)")
 L2_FLUSH_BYTES = 512 << 20
+ORACLE_PAIRS = [(1, 2), (2, 3)]  # the pairs the sequential oracle finishes at full size in about a minute
 
 
 def parse():
@@ -46,6 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="headline step only (no config 3-5 measurements)")
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
@@ -128,19 +133,58 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------------------------------------------
-# reference arm: the sequential CPU oracle on a bounded sample
+# the sequential CPU oracle (reference arm and cpu_baseline leg)
 # -------------------------------------------------------------------------------------------------
 
-def cpu_oracle_sample(scale: int = 15):
-    """One bounded oracle run: (2,3) exact core numbers + definitional hierarchy of R-MAT scale
-    `scale` EF16 seed 2, one host thread.  Returns (s-cliques, seconds)."""
+def _oracle_pairs_worker(scale: int, pairs, conn):
+    """Child process (spawned before any GPU call): the oracle's exact core numbers + hierarchy of
+    R-MAT <scale> EF16 seed 2 for each pair, one host thread; sends per-pair (n_s, seconds, core
+    bytes) back."""
+    try:
+        import oracle
+        from paper_2306_08623_gb300 import graphgen as gg
+        oracle.build()
+        off, adj = gg.rmat(scale, 16, 2)
+        out = {}
+        for r, s in pairs:
+            t0 = time.perf_counter()
+            res = oracle.nucleus(off, adj, r, s, hier="def")
+            dt = time.perf_counter() - t0
+            out["%d,%d" % (r, s)] = {"n_s": int(res["n_s"]), "seconds": dt, "core": res["core"].tobytes(),
+                                     "nodes": int(len(res["node_parent"]))}
+        conn.send(out)
+    except Exception as exc:  # reported in the JSON line, never fatal for the GPU arm
+        conn.send({"error": repr(exc)})
+    conn.close()
+
+
+def start_oracle(scale: int, pairs):
+    ctx = mp.get_context("spawn")
+    parent, child = ctx.Pipe(duplex=False)
+    p = ctx.Process(target=_oracle_pairs_worker, args=(scale, pairs, child), daemon=True)
+    p.start()
+    child.close()
+    return p, parent
+
+
+def cpu_oracle_sample():
+    """One bounded oracle step of the reference arm: the (1,2) hierarchy of the benchmark graph
+    itself (R-MAT 18) and the (2,3) hierarchy of R-MAT 15 EF16 seed 2 (the same generator at 1/8 of
+    the size: the full-size (2,3) oracle takes about two minutes).  Returns (s-cliques, seconds)."""
     import oracle
     from paper_2306_08623_gb300 import graphgen as gg
-    off, adj = gg.rmat(scale, 16, 2)
-    t0 = time.perf_counter()
-    res = oracle.nucleus(off, adj, 2, 3, hier="def")
-    dt = time.perf_counter() - t0
-    return res["n_s"], dt
+    tot_s, tot_t = 0, 0.0
+    for scale, (r, s) in [(18, (1, 2)), (15, (2, 3))]:
+        off, adj = gg.rmat(scale, 16, 2)
+        t0 = time.perf_counter()
+        res = oracle.nucleus(off, adj, r, s, hier="def")
+        tot_t += time.perf_counter() - t0
+        tot_s += res["n_s"]
+    return tot_s, tot_t
+
+
+REF_SAMPLE = ("per step: the (1,2) hierarchy of R-MAT 18 EF16 seed 2 (the benchmark graph) and the (2,3) hierarchy "
+              "of R-MAT 15 EF16 seed 2, exact core numbers + definitional hierarchy, sequential oracle, one host thread")
 
 
 def run_reference(args):
@@ -149,22 +193,20 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    scale = 15
     for _ in range(args.warmup):
-        cpu_oracle_sample(scale)
+        cpu_oracle_sample()
     tot_s, tot_t = 0, 0.0
     for _ in range(args.steps):
-        ns, dt = cpu_oracle_sample(scale)
+        ns, dt = cpu_oracle_sample()
         tot_s += ns
         tot_t += dt
     value = tot_s / tot_t
-    sample = "RMAT scale %d EF16 seed 2, exact (2,3) core numbers + hierarchy, sequential oracle" % scale
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample, "l2": "inputs > L2 not needed (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": REF_SAMPLE, "l2": "CPU run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": REF_SAMPLE},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -174,33 +216,43 @@ def run_reference(args):
 # our arm
 # -------------------------------------------------------------------------------------------------
 
-def pair_report(info: dict, peel_ms: dict, hier_ms: dict, alt_ms: dict, peak_gbs: float) -> dict:
+def algorithmic_peel_bytes(stats: dict) -> int:
+    """Bytes the peel must move (the §8(d) count, from the peel's own device counters):
+    B = 4 E_scan + 8 U_cnt + 16 P_hash + 8 N_link + 4 F, with E_scan = list elements read by the
+    re-listing (adjacency, per-edge triangle lists and the out-lists expanded from them: every
+    4-byte element read), U_cnt = count decrements (atomic read + write), P_hash = probes of the
+    global triangle hash (16-byte slots), N_link = link-efficient steps (uf + L entries), and F =
+    frontier traffic (12 bytes per frontier entry: id, round stamp, value) plus every round stamp
+    or core number of a member read while re-listing (4 bytes each)."""
+    return (4 * stats["scan_elements"] + 8 * stats["decrements"] + 16 * stats["hash_probes"]
+            + 8 * stats["link_calls"] + 12 * stats["frontier_total"] + 4 * stats["stamp_reads"])
+
+
+def pair_report(info: dict, peel_ms: dict, hier_ms: dict, alt_ms: dict, peak_gbs: float, oracle_res: dict) -> dict:
     """Per (r,s) pair of one step: sizes, the hierarchy builder, peel and hierarchy times, the
-    other builder's time, s-cliques peeled per second and the peel's algorithmic GB/s and
-    fraction of the HBM peak (every s-clique dies exactly once in the peel)."""
+    other builder's time, s-cliques peeled per second, the peel's algorithmic GB/s and fraction of
+    the HBM peak, and (where the oracle ran on the same pair) its time and the GPU speed-up."""
     out = {}
     for k, v in info.items():
         other = "te" if METHOD[k] == "el" else "el"
-        gbs = algorithmic_peel_bytes(v["stats"], *k) / (peel_ms[k] / 1000.0) / 1e9 if peel_ms[k] > 0 else 0.0
-        out["%d,%d" % k] = {
-            "n_r": v["n_r"], "n_s": v["n_s"], "nodes": v["n_nodes"], "rounds": v["stats"]["rounds"],
-            "method": METHOD[k], "peel_ms": round(peel_ms[k], 3), "hierarchy_ms": round(hier_ms[k], 3),
-            other + "_peel_and_hierarchy_ms": round(alt_ms[k], 3),
-            "s_cliques_peeled_per_s": v["n_s"] / (peel_ms[k] / 1000.0) if peel_ms[k] > 0 else 0.0,
-            "peel_algorithmic_gbs": round(gbs, 3), "peel_frac_of_hbm_peak": gbs / peak_gbs,
-        }
+        ab = algorithmic_peel_bytes(v["stats"])
+        gbs = ab / (peel_ms[k] / 1000.0) / 1e9 if peel_ms[k] > 0 else 0.0
+        d = {"n_r": v["n_r"], "n_s": v["n_s"], "nodes": v["n_nodes"], "rounds": v["stats"]["rounds"],
+             "method": METHOD[k], "peel_ms": round(peel_ms[k], 3), "hierarchy_ms": round(hier_ms[k], 3),
+             other + "_peel_and_hierarchy_ms": round(alt_ms.get(k, float("nan")), 3),
+             "s_cliques_peeled_per_s": v["n_s"] / (peel_ms[k] / 1000.0) if peel_ms[k] > 0 else 0.0,
+             "peel_algorithmic_bytes": ab, "peel_algorithmic_gbs": round(gbs, 3), "peel_frac_of_hbm_peak": gbs / peak_gbs}
+        key = "%d,%d" % k
+        if oracle_res and key in oracle_res:
+            o = oracle_res[key]
+            gpu_s = (peel_ms[k] + hier_ms[k]) / 1000.0
+            d["oracle_seconds"] = round(o["seconds"], 3)
+            d["gpu_peel_and_hierarchy_vs_oracle"] = o["seconds"] / gpu_s if gpu_s > 0 else None
+            d["oracle_core_equal"] = o.get("core_equal")
+        elif k not in ORACLE_PAIRS:
+            d["oracle_seconds"] = "not run (the sequential oracle enumerates 2.3e9 4-cliques: hours)"
+        out[key] = d
     return out
-
-
-def algorithmic_peel_bytes(stats: dict, r: int, s: int) -> int:
-    """Bytes the peel must move, from its own counters: every scanned adjacency entry (4 B), the
-    round stamps of the other members of every re-listed s-clique (4 B each), every count
-    decrement (4 B read + 4 B write), every triangle-table probe (one 16 B slot), every
-    link-efficient call (uf + L entries, 8 B), every frontier entry (id + round + core, 12 B)."""
-    from math import comb
-    C = comb(s, r)
-    return (4 * stats["scan_elements"] + 4 * (C - 1) * stats["s_cliques_listed"] + 8 * stats["decrements"]
-            + 16 * stats["hash_probes"] + 8 * stats["link_calls"] + 12 * stats["frontier_total"])
 
 
 def reduce_max(value: float, device=None) -> float:
@@ -220,13 +272,17 @@ def whole_job_rate(units_per_rank: int, world: int, steps: int, max_ms: float) -
 
 
 def run_ours(args):
+    rank, world, local = dist_env()
+    oracle_proc = None
+    if rank == 0 and world == 1 and args.scale == 18:
+        oracle_proc = start_oracle(18, ORACLE_PAIRS)  # before the first GPU call
+
     import numpy as np
     import torch
 
     import paper_2306_08623_gb300.nucleus as nc
     from paper_2306_08623_gb300 import graphgen as gg
 
-    rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -307,6 +363,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     value = whole_job_rate(n_s_tot, world, args.steps, total_ms)
 
+    # the core numbers of the oracle pairs, kept for the comparison with the oracle's
+    cores = {}
+    o_k = nc.build_orientation(d_off, d_adj)
+    for r, s in ORACLE_PAIRS:
+        ri_k = nc.index_r_cliques(o_k, r)
+        cnt_k, _ = nc.count_s_cliques(o_k, ri_k, s)
+        cores[(r, s)] = nc.peel_cores(o_k, ri_k, s, cnt_k)["core"].cpu().numpy().view(np.uint32)
+        del ri_k, cnt_k
+    del o_k
+
     # beside the timed step, once: each pair's hierarchy built the other way (anh-el <-> anh-te)
     alt_ms = {}
     o2 = nc.build_orientation(d_off, d_adj)
@@ -335,16 +401,16 @@ def run_ours(args):
     hier_ms = {k[1:]: v for k, v in ev_ms.items() if k[0] == "hier"}
     dom = max(peel_ms, key=peel_ms.get)
     peak, peak_kind = measured_peaks()
-    alg_bytes = algorithmic_peel_bytes(info[dom]["stats"], *dom)
+    alg_bytes = algorithmic_peel_bytes(info[dom]["stats"])
     achieved = alg_bytes / (peel_ms[dom] / 1000.0) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "peel_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tt = json.load(f)
-        if (tt.get("kernel") == "k_peel<%d,%d,true>" % dom and tt.get("method") == METHOD[dom]
-                and tt.get("source_hash") == _source_hash(dom)):
-            traffic = tt.get("dram_bytes_per_launch")
+        rec = tt.get("%d,%d" % dom) if isinstance(tt, dict) else None
+        if rec and rec.get("method") == METHOD[dom] and rec.get("source_hash") == _source_hash(dom):
+            traffic = rec.get("dram_bytes_per_launch")
 
     # end to end through host buffers: H2D of the CSR from pinned memory, the path, D2H of
     # core / parent / label of every pair
@@ -373,17 +439,43 @@ def run_ours(args):
     e2e_total = reduce_max(sum(e2e_ms), dev)
     e2e_value = whole_job_rate(n_s_tot, world, args.steps, e2e_total)
 
-    cpu = None
-    if rank == 0 and world == 1:
-        import oracle
-        oracle.build()
-        ns, dt = cpu_oracle_sample(15)
-        cpu = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "RMAT scale 15 EF16 seed 2, exact (2,3) core numbers + hierarchy, one host thread "
-                         "(%d of %d cores), %.1f s" % (1, os.cpu_count() or 0, dt)}
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.scale == 18:
+        del flush
+        torch.cuda.empty_cache()
+        extras = {}
+        for name, fn in (("cl4m", measure_cl4m), ("batch512", measure_batch512), ("approx", measure_approx)):
+            t0 = time.perf_counter()
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # an extra measurement never voids the headline line
+                extras[name] = {"error": repr(exc)[:400]}
+            extras[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+            torch.cuda.empty_cache()
+
+    cpu, oracle_res = None, {}
+    if oracle_proc is not None:
+        proc, conn = oracle_proc
+        got = conn.recv() if conn.poll(1800) else {"error": "oracle did not finish in 30 min"}
+        proc.join(timeout=10)
+        if "error" in got:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": got["error"]}
+        else:
+            for key, o in got.items():
+                rs = tuple(int(x) for x in key.split(","))
+                o["core_equal"] = bool(np.array_equal(np.frombuffer(o.pop("core"), dtype=np.uint32), cores[rs]))
+                oracle_res[key] = o
+            ns = sum(o["n_s"] for o in oracle_res.values())
+            secs = sum(o["seconds"] for o in oracle_res.values())
+            cpu = {"value": ns / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "the (1,2) and (2,3) exact hierarchies (core numbers + definitional hierarchy) of the "
+                             "benchmark graph itself, sequential oracle, one host thread of %d, run in a spawned "
+                             "process beside the GPU work; %.1f s; (2,4) and (3,4) not run (2.3e9 4-cliques: hours)"
+                             % (os.cpu_count() or 0, secs),
+                   "per_pair_seconds": {k: round(o["seconds"], 3) for k, o in oracle_res.items()}}
 
     if rank == 0:
-        per_pair = pair_report(info, peel_ms, hier_ms, alt_ms, peak)
+        per_pair = pair_report(info, peel_ms, hier_ms, alt_ms, peak, oracle_res)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -396,13 +488,16 @@ def run_ours(args):
                          "kernel": "k_peel<%d,%d,true> %s (%s peak)" % (dom[0], dom[1],
                                                                         "with link-efficient" if METHOD[dom] == "el"
                                                                         else "core numbers only", peak_kind),
-                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": peel_ms[dom]},
+                         "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": peel_ms[dom],
+                         "bytes_formula": "4 E_scan + 8 U_cnt + 16 P_hash + 8 N_link + 12 frontier + 4 stamp reads"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(off.nbytes + adj.nbytes),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_total / args.steps},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        if extras is not None:
+            line["configs_beside"] = extras
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -410,7 +505,7 @@ def run_ours(args):
 
 
 # -------------------------------------------------------------------------------------------------
-# further workloads (one JSON line each; not the headline step)
+# the other configurations (measured once each beside the headline step, or alone with --workload)
 # -------------------------------------------------------------------------------------------------
 
 def _ev():
@@ -426,12 +521,17 @@ def _ms(a, b):
     return a.elapsed_time(b)
 
 
-def run_cl4m(args):
+def _spread(xs):
+    import numpy as np
+    return {"median": float(np.median(xs)), "min": float(np.min(xs)), "max": float(np.max(xs)), "n": len(xs)}
+
+
+def measure_cl4m(warmup: int = 1, steps: int = 5) -> dict:
     """Chung-Lu n = 4M, exponent 2.1, mean degree 20, plus 400 groups x 5 nested planted cliques of
-    size U[10,60] (2,000 cliques), seed 3.  Counting time for (2,3) and (3,4) with the plain
-    work distribution, the degree-cost partition and the learned-cost partition (MLP trained on
-    the costs measured on a second graph of the same recipe, seed 4, n = 1M); all three must give
-    identical counts."""
+    size U[10,60] (2,000 cliques), seed 3: counting time of (2,3) and (3,4) with the plain work
+    distribution, the degree-cost schedule and the learned-cost schedule (MLP trained on the costs
+    measured on a second graph of the same recipe, seed 4, n = 1M); all three give identical counts
+    (asserted).  Median and min-max over `steps` runs."""
     import numpy as np
     import torch
 
@@ -461,13 +561,12 @@ def run_cl4m(args):
         infer_ms = _ms(a, b)
         dcost = nc.degree_cost(o, s)
         measured = nc.listing_cost(o, ri, s)
-        # correlation of the predictions with the measured cost on the benchmark graph
         lm, lp, ld = (torch.log1p(x).double() for x in (measured, pred, dcost))
         corr = lambda x, y: float(((x - x.mean()) * (y - y.mean())).mean() / (x.std() * y.std() + 1e-12))
         times = {"plain": [], "degree": [], "learned": []}
         ref, n_s0 = nc.count_s_cliques(o, ri, s)
         ref = ref.clone()
-        for _ in range(args.warmup + args.steps):
+        for _ in range(warmup + steps):
             for mode in ("plain", "degree", "learned"):
                 a = _ev()
                 if mode == "plain":
@@ -477,25 +576,53 @@ def run_cl4m(args):
                 b = _ev()
                 times[mode].append(_ms(a, b))
                 assert ns == n_s0 and torch.equal(cnt, ref), "partition changed the counts"
-        med = {k: float(np.median(v[args.warmup:])) for k, v in times.items()}
-        res["%d,%d" % (r, s)] = {"n_r": ri.n_r, "n_s": n_s0, "count_ms": med, "mlp_train_ms": train_ms,
-                                 "mlp_final_mse_log": loss, "mlp_infer_ms": infer_ms,
-                                 "corr_log_cost": {"learned": corr(lm, lp), "degree": corr(lm, ld)}}
+        res["%d,%d" % (r, s)] = {"n_r": ri.n_r, "n_s": n_s0, "count_ms": {k: _spread(v[warmup:]) for k, v in times.items()},
+                                 "mlp_train_ms": train_ms, "mlp_final_mse_log": loss, "mlp_infer_ms": infer_ms,
+                                 "corr_log_cost": {"learned": corr(lm, lp), "degree": corr(lm, ld)},
+                                 "identical_counts": True}
         del ri, feats, pred, dcost, measured, ref
-    tot = {k: sum(v["count_ms"][k] for v in res.values()) for k in ("plain", "degree", "learned")}
-    line = {"metric": "s-clique counting time, learned vs degree work partition", "value": tot["learned"],
-            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "dtype": "int32 counts; bf16 weights / fp32 accumulation (MLP)", "data": "synthetic",
-            "config": {"workload": "Chung-Lu n=4194304 beta 2.1 mean degree 20 + 2000 planted nested cliques "
-                                   "U[10,60], seed 3; estimator trained on the same recipe n=1048576 seed 4",
-                       "pairs": res, "total_ms": tot}}
-    print(json.dumps(line), flush=True)
+    tot = {k: sum(v["count_ms"][k]["median"] for v in res.values()) for k in ("plain", "degree", "learned")}
+    return {"metric": "s-clique counting time, learned vs degree vs plain work distribution", "unit": "ms",
+            "workload": "Chung-Lu n=4194304 beta 2.1 mean degree 20 + 2000 planted nested cliques U[10,60], seed 3; "
+                        "estimator trained on the same recipe n=1048576 seed 4",
+            "pairs": res, "total_median_ms": tot}
 
 
-def run_batch512(args):
+def _same_forest(pa, la, pb, lb, n_r) -> bool:
+    """Whether two trees over the same n_r leaves are equal up to node numbering (device tensors):
+    the leaf-to-node maps must pair A's and B's nodes one to one (every node has leaves of its
+    own), and labels and parents must agree under that pairing."""
+    import torch
+    a = pa[:n_r].long()
+    b = pb[:n_r].long()
+    if not torch.equal(a < 0, b < 0):
+        return False
+    m = a >= 0
+    na, nb = pa.numel() - n_r, pb.numel() - n_r
+    if not bool(m.any()):
+        return na == 0 and nb == 0
+    key = torch.unique(a[m] * (nb + 1) + b[m])
+    ka, kb = key // (nb + 1), key % (nb + 1)
+    if key.numel() != na or key.numel() != nb or torch.unique(ka).numel() != na or torch.unique(kb).numel() != nb:
+        return False
+    if not torch.equal(la[ka].long(), lb[kb].long()):
+        return False
+    amap = torch.full((na,), -1, dtype=torch.long, device=pa.device)
+    amap[ka] = kb
+    par_a = pa[n_r + ka].long()
+    par_b = pb[n_r + kb].long()
+    mapped = torch.where(par_a >= 0, amap[par_a.clamp(min=0)], torch.full_like(par_a, -1))
+    return bool(torch.equal(mapped, par_b))
+
+
+def measure_batch512(warmup: int = 0, steps: int = 1) -> dict:
     """512 graphs, seeds 1000..1511 (n log-uniform in [1e3, 2e5], mean degree U[8,40], families
     Erdos-Renyi / R-MAT / Chung-Lu + planted cliques): exact (2,3) and (3,4) hierarchies of every
-    graph, one by one versus as one batched union (one persistent peel launch per pair)."""
+    graph.  One by one: the whole path per graph (hierarchy, auto builder).  Batched: the disjoint
+    union's orientation and index, then counts, peel (one persistent launch) and construct-tree
+    replayed from a CUDA graph.  Every graph's core numbers and canonical hierarchy are compared
+    between the two forms; the peel knobs are picked by the project's autotuner first."""
+    import numpy as np
     import torch
 
     import paper_2306_08623_gb300.nucleus as nc
@@ -505,42 +632,144 @@ def run_batch512(args):
     graphs = [gg.batch_member(1000 + i) for i in range(n_graphs)]
     dev = [(torch.from_numpy(o).cuda(), torch.from_numpy(a).cuda()) for o, a in graphs]
     tot_m = sum(len(a) // 2 for _, a in graphs)
+    off_u, adj_u, vbase = nc.batch_union(dev)
+    o_u = nc.build_orientation(off_u, adj_u)
+    ri23 = nc.index_r_cliques(o_u, 2)
+    buf23 = nc.hierarchy_buffers(ri23)
+    tuned = nc.autotune_peel(lambda: nc.hierarchy_enqueue(o_u, ri23, 3, buf23), max_groups=(64, 1024),
+                             task_items=(0, -1))
+    del buf23, ri23, o_u
     res = {}
-    # the batched form's scheduling knobs, picked by timing the batched (2,3) hierarchy once each
-    off_u, adj_u, _ = nc.batch_union(dev)
-    tuned = nc.autotune_peel(lambda: nc.hierarchy(off_u, adj_u, 2, 3), max_groups=(64, 1024), task_items=(0, -1))
-    del off_u, adj_u
     for r, s in [(2, 3), (3, 4)]:
         t_one, t_batch = [], []
-        n_s = 0
-        for it in range(args.warmup + args.steps):
+        for it in range(warmup + steps):
+            outs = []
             a = _ev()
-            n_s = 0
             for off_t, adj_t in dev:
-                out = nc.hierarchy(off_t, adj_t, r, s)
-                n_s += out["n_s"]
+                h = nc.hierarchy(off_t, adj_t, r, s, method="auto")
+                outs.append({k: h[k] for k in ("n_r", "core", "parent", "label", "n_nodes")})
+                del h  # frees the graph's orientation and index
             b = _ev()
             t_one.append(_ms(a, b))
+            if it < warmup + steps - 1:
+                del outs
             a = _ev()
-            off_u, adj_u, vbase = nc.batch_union(dev)
-            out = nc.hierarchy(off_u, adj_u, r, s)
+            off_u, adj_u, vb = nc.batch_union(dev)
+            o_u = nc.build_orientation(off_u, adj_u)
+            ri = nc.index_r_cliques(o_u, r)
+            buf = nc.hierarchy_buffers(ri)
             b = _ev()
-            t_batch.append(_ms(a, b))
-            assert out["n_s"] == n_s
-        res["%d,%d" % (r, s)] = {"n_s": n_s, "one_by_one_ms": sum(t_one[args.warmup:]) / args.steps,
-                                 "batched_ms": sum(t_batch[args.warmup:]) / args.steps}
-    tot_one = sum(v["one_by_one_ms"] for v in res.values())
-    tot_b = sum(v["batched_ms"] for v in res.values())
-    line = {"metric": "512-graph exact hierarchy batch time", "value": tot_b, "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": "512 graphs seeds 1000-1511, %d edges in total, exact (2,3) "
-                                                        "and (3,4)" % tot_m, "pairs": res,
-                                            "autotuned": {"max_group": tuned["best"][0],
-                                                          "task_items": tuned["best"][1],
-                                                          "times_ms": {"%d,%d" % k: v for k, v in
-                                                                       tuned["times_ms"].items()}},
-                                            "one_by_one_ms": tot_one, "speedup": tot_one / tot_b}}
+            t_prep = _ms(a, b)
+            g = nc.capture_hierarchy(o_u, ri, s, buf)  # one eager run, then the capture (not timed)
+            for t in buf.values():
+                t.fill_(-1)
+            c = _ev()
+            g.replay()
+            d = _ev()
+            t_batch.append(t_prep + _ms(c, d))
+            status = buf["res"].cpu().numpy()
+            assert status[0] == 0, status
+        # every graph's slice of the union equals its own run: core numbers, and the hierarchy up to
+        # node numbering (the one-by-one trees laid side by side, node ids shifted per graph)
+        rb = nc.rindex_bases(ri, vb)
+        n_r = ri.n_r
+        nn_u = int(status[2])
+        assert [int(rb[i + 1] - rb[i]) for i in range(n_graphs)] == [o["n_r"] for o in outs]
+        core_b = torch.cat([o["core"] for o in outs])
+        nbase = np.concatenate([[0], np.cumsum([o["n_nodes"] for o in outs])])
+        leaf_b = torch.cat([torch.where(o["parent"][: o["n_r"]] >= 0, o["parent"][: o["n_r"]] + int(nbase[i]), -1)
+                            for i, o in enumerate(outs)])
+        node_b = torch.cat([torch.where(o["parent"][o["n_r"]:] >= 0, o["parent"][o["n_r"]:] + int(nbase[i]), -1)
+                            for i, o in enumerate(outs)])
+        label_b = torch.cat([o["label"] for o in outs])
+        same = torch.equal(buf["core"][:n_r], core_b) and _same_forest(
+            buf["parent"][: n_r + nn_u], buf["label"][:nn_u], torch.cat([leaf_b, node_b]), label_b, n_r)
+        assert same, "the batched hierarchies differ from the one-by-one ones"
+        res["%d,%d" % (r, s)] = {"n_s": int(status[1]), "one_by_one_ms": _spread(t_one[warmup:]),
+                                 "batched_ms": _spread(t_batch[warmup:]), "graphs_identical": n_graphs}
+        del buf, g, ri, o_u, off_u, adj_u, outs, core_b, leaf_b, node_b, label_b
+        torch.cuda.empty_cache()
+    tot_one = sum(v["one_by_one_ms"]["median"] for v in res.values())
+    tot_b = sum(v["batched_ms"]["median"] for v in res.values())
+    return {"metric": "512-graph exact hierarchy batch time", "unit": "ms",
+            "workload": "512 graphs seeds 1000-1511, %d edges in total, exact (2,3) and (3,4)" % tot_m,
+            "pairs": res, "one_by_one_ms": tot_one, "batched_ms": tot_b, "speedup": tot_one / tot_b,
+            "batched_form": "disjoint union, its orientation and index (timed), then counts + one persistent peel "
+                            "launch + construct-tree replayed from a CUDA graph (timed; capturing it is not)",
+            "autotuned": {"max_group": tuned["best"][0], "task_items": tuned["best"][1],
+                          "times_ms": {"%d,%d" % k: v for k, v in tuned["times_ms"].items()}}}
+
+
+def measure_approx(steps: int = 1) -> dict:
+    """Approximate core numbers (Alg. 2) beside the exact GPU run: (2,3) on R-MAT 22 EF16 seed 4,
+    (3,4) on R-MAT 20 EF16 seed 3, delta in {0.1, 0.5}: time, speedup over the exact peel (core
+    numbers only, the same re-listing), and the mean / max multiplicative error over r-cliques of
+    exact core >= 1, with Thm. 2's bound checked for every r-clique."""
+    import numpy as np
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    out = {}
+    for scale, seed, r, s in [(22, 4, 2, 3), (20, 3, 3, 4)]:
+        off, adj = gg.rmat(scale, 16, seed)
+        o = nc.build_orientation(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda())
+        del off, adj
+        ri = nc.index_r_cliques(o, r)
+        cnt, n_s = nc.count_s_cliques(o, ri, s)
+        nc.peel_cores(o, ri, s, cnt)  # warm-up
+        a = _ev()
+        pk = nc.peel_cores(o, ri, s, cnt, stats=True)
+        b = _ev()
+        exact_ms = _ms(a, b)
+        core = pk["core"].double()
+        entry = {"n_r": ri.n_r, "n_s": n_s, "exact_peel_ms": exact_ms, "exact_rounds": pk["stats"]["rounds"]}
+        del pk
+        nz = core > 0
+        for delta in (0.1, 0.5):
+            ts = []
+            for _ in range(max(1, steps)):
+                a = _ev()
+                ap = nc.approx_nucleus(o, ri, s, delta, cnt, stats=True)
+                b = _ev()
+                ts.append(_ms(a, b))
+            ratio = ap["approx"].double()[nz] / core[nz]
+            C = {(2, 3): 3, (3, 4): 4}[(r, s)]
+            bound = (C + delta) * (1 + delta)
+            within = bool((ratio >= 1).all() and (ratio <= bound + 1e-9).all() and (ap["approx"][~nz] == 0).all())
+            assert within, "approximation outside Thm. 2's bound"
+            entry["delta_%g" % delta] = {"approx_peel_ms": float(np.median(ts)), "rounds": ap["stats"]["rounds"],
+                                         "speedup_vs_exact": exact_ms / float(np.median(ts)),
+                                         "mean_err": float(ratio.mean()), "max_err": float(ratio.max()),
+                                         "bound": bound, "within_bound": within}
+            del ap
+        out["RMAT%d (%d,%d)" % (scale, r, s)] = entry
+        del ri, cnt, core, o
+        torch.cuda.empty_cache()
+    return {"metric": "approximate vs exact core numbers", "unit": "ms",
+            "workload": "R-MAT 22 EF16 seed 4 (2,3); R-MAT 20 EF16 seed 3 (3,4); delta 0.1 and 0.5", "results": out}
+
+
+def run_cl4m(args):
+    line = {"metric": "s-clique counting time, learned vs degree work partition", "n_gpus": 1,
+            "data": "synthetic", "higher_is_better": False}
+    r = measure_cl4m(args.warmup, args.steps)
+    line.update({"value": r["total_median_ms"]["learned"], "unit": "ms", "config": r})
     print(json.dumps(line), flush=True)
+
+
+def run_batch512(args):
+    r = measure_batch512(args.warmup, args.steps)
+    print(json.dumps({"metric": r["metric"], "value": r["batched_ms"], "unit": "ms", "higher_is_better": False,
+                      "n_gpus": 1, "data": "synthetic", "config": r}), flush=True)
+
+
+def run_approx(args):
+    r = measure_approx(args.steps)
+    v = r["results"]["RMAT22 (2,3)"]["delta_0.1"]["speedup_vs_exact"]
+    print(json.dumps({"metric": r["metric"], "value": v, "unit": "x speedup (RMAT22 (2,3), delta 0.1)",
+                      "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "config": r}), flush=True)
 
 
 def run_peel1(args):
@@ -560,8 +789,8 @@ def run_peel1(args):
         b = _ev()
     line = {"metric": "exact hierarchy time", "value": _ms(a, b), "unit": "ms", "higher_is_better": False,
             "config": {"workload": "R-MAT scale %d EF16 seed 2 (%d,%d) method %s" % (args.scale, r, s, args.method),
-                       "n_r": res["n_r"],
-                       "n_s": res["n_s"], "nodes": res["n_nodes"], "stats": res["stats"]}}
+                       "n_r": res["n_r"], "n_s": res["n_s"], "nodes": res["n_nodes"], "stats": res["stats"],
+                       "algorithmic_peel_bytes": algorithmic_peel_bytes(res["stats"])}}
     print(json.dumps(line), flush=True)
 
 
@@ -610,63 +839,15 @@ def run_approx_hier(args):
     print(json.dumps(line), flush=True)
 
 
-def run_approx(args):
-    """Approximate core numbers (Alg. 2) beside the exact GPU run: (2,3) on R-MAT 22 EF16 seed 4,
-    (3,4) on R-MAT 20 EF16 seed 3, delta in {0.1, 0.5}: time, speedup over the exact peel, and the
-    mean / max multiplicative error over r-cliques of exact core >= 1."""
-    import numpy as np
-    import torch
-
-    import paper_2306_08623_gb300.nucleus as nc
-    from paper_2306_08623_gb300 import graphgen as gg
-    nc.lib()
-    out = {}
-    for scale, seed, r, s in [(22, 4, 2, 3), (20, 3, 3, 4)]:
-        off, adj = gg.rmat(scale, 16, seed)
-        o = nc.build_orientation(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda())
-        del off, adj
-        ri = nc.index_r_cliques(o, r)
-        cnt, n_s = nc.count_s_cliques(o, ri, s)
-        a = _ev()
-        pk = nc.peel_and_link(o, ri, s, cnt, stats=True)
-        b = _ev()
-        exact_ms = _ms(a, b)
-        core = pk["core"].double()
-        entry = {"n_r": ri.n_r, "n_s": n_s, "exact_peel_ms": exact_ms, "exact_rounds": pk["stats"]["rounds"]}
-        del pk
-        nz = core > 0
-        for delta in (0.1, 0.5):
-            ts = []
-            for _ in range(max(1, args.steps)):
-                a = _ev()
-                ap = nc.approx_nucleus(o, ri, s, delta, cnt, stats=True)
-                b = _ev()
-                ts.append(_ms(a, b))
-            ratio = ap["approx"].double()[nz] / core[nz]
-            C = {(2, 3): 3, (3, 4): 4}[(r, s)]
-            entry["delta_%g" % delta] = {"approx_peel_ms": float(np.median(ts)), "rounds": ap["stats"]["rounds"],
-                                         "speedup_vs_exact": exact_ms / float(np.median(ts)),
-                                         "mean_err": float(ratio.mean()), "max_err": float(ratio.max()),
-                                         "bound": (C + delta) * (1 + delta),
-                                         "within_bound": bool((ratio >= 1).all() and (ratio <= (C + delta) * (1 + delta) + 1e-9).all())}
-        out["RMAT%d (%d,%d)" % (scale, r, s)] = entry
-        del ri, cnt, core, o
-        torch.cuda.empty_cache()
-    line = {"metric": "approximate vs exact core numbers", "value": out["RMAT22 (2,3)"]["delta_0.1"]["speedup_vs_exact"],
-            "unit": "x speedup (RMAT22 (2,3), delta 0.1)", "higher_is_better": True, "n_gpus": 1, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": "R-MAT 22 EF16 seed 4 (2,3); R-MAT 20 EF16 seed 3 (3,4)",
-                                            "results": out}}
-    print(json.dumps(line), flush=True)
-
-
 def _source_hash(pair) -> str:
     """Hash of the sources the peel kernel of one (r,s) pair is compiled from (a traffic record
     counts only for the kernel it was taken on)."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2306_08623_gb300", "csrc")
-    for path in (os.path.join(csrc, "nh_peel.cuh"), os.path.join(csrc, "nh_internal.cuh"),
-                 os.path.join(csrc, "nh_peel_rs%d%d.cu" % pair), os.path.join(ROOT, "include", "nucleus.h")):
+    for path in (os.path.join(csrc, "nh_peel.cuh"), os.path.join(csrc, "nh_relist24.cuh"),
+                 os.path.join(csrc, "nh_internal.cuh"), os.path.join(csrc, "nh_peel_rs%d%d.cu" % pair),
+                 os.path.join(ROOT, "include", "nucleus.h")):
         with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

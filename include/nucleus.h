@@ -21,7 +21,9 @@
  *    (r=1) is vertex i, of (r=2) the i-th edge (u<v) in lexicographic order, of (r=3) the i-th
  *    triangle (a<b<c) in lexicographic order.
  *  - Supported (r,s): (1,2), (1,3), (2,3), (2,4), (3,4).  Others return NH_ERR_UNSUPPORTED.
- *  - Counts and core numbers are uint32; the configurations stay far below 2^32.
+ *  - Counts and core numbers are uint32.  Counting checks every increment and returns
+ *    NH_ERR_COUNT_OVERFLOW when an s-clique-degree would exceed 2^32 - 1 (core numbers and
+ *    approximate values never exceed the s-clique-degree).
  *  - Return value: NH_OK (0) or one of the NH_ERR_* codes below.  A code returned by a device-side
  *    check (table full, bounded wait expired, bad index) leaves the context usable.
  */
@@ -43,6 +45,7 @@ extern "C" {
 #define NH_ERR_UNSUPPORTED 6  /* (r,s) outside the supported set                              */
 #define NH_ERR_CUDA 7         /* a CUDA runtime call failed                                   */
 #define NH_ERR_INTERNAL 8     /* a device-side consistency check failed (lookup miss)          */
+#define NH_ERR_COUNT_OVERFLOW 9 /* an s-clique-degree exceeds 2^32 - 1 (counts are uint32)     */
 
 typedef struct nh_oriented nh_oriented;
 typedef struct nh_rindex nh_rindex;
@@ -89,7 +92,8 @@ void nh_rindex_free(nh_rindex* ri);
  * (s-clique-degree, §3), for every r-clique R, found by recursive intersection of out-lists of
  * the orientation so that each s-clique is listed once.  cnt: uint32[n_r] (overwritten).
  * *n_s (host, may be NULL) receives the number of s-cliques.
- * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_INTERNAL, NH_ERR_CUDA. */
+ * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_INTERNAL, NH_ERR_COUNT_OVERFLOW,
+ * NH_ERR_CUDA. */
 int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt,
                        uint64_t* n_s, void* stream);
 

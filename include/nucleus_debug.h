@@ -21,9 +21,13 @@ extern "C" {
 /* capacity, in slots (a power of two), of the edge table (nh_build_orientation) and of the
  * triangle table (nh_index_r_cliques, r = 3) built from now on; 0 = automatic (load <= 0.5) */
 #define NH_INJECT_TABLE_CAP 2
+/* value every s-clique-degree starts from before counting (nh_count_s_cliques and the counting
+ * step of nh_hierarchy_enqueue, s >= 3) in place of 0, so that a small graph reaches the uint32
+ * limit: counting then returns NH_ERR_COUNT_OVERFLOW; 0 = off */
+#define NH_INJECT_COUNT_BASE 3
 
-/* Set one injection.  value >= 0 (NH_INJECT_TABLE_CAP: 0 or a power of two).  Returns NH_OK or
- * NH_ERR_INVALID (unknown `what`, bad value; nothing changed). */
+/* Set one injection.  value >= 0 (NH_INJECT_TABLE_CAP: 0 or a power of two; NH_INJECT_COUNT_BASE:
+ * < 2^32).  Returns NH_OK or NH_ERR_INVALID (unknown `what`, bad value; nothing changed). */
 int nh_debug_inject(int what, int64_t value);
 
 /* Round trace of the persistent peel kernels (nh_peel_and_link, nh_approx_nucleus): when set, the

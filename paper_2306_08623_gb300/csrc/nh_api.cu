@@ -21,6 +21,7 @@ extern "C" const char* nh_status_string(int status) {
     case NH_ERR_UNSUPPORTED: return "unsupported (r,s) or device";
     case NH_ERR_CUDA: return "CUDA runtime error";
     case NH_ERR_INTERNAL: return "device consistency check failed";
+    case NH_ERR_COUNT_OVERFLOW: return "s-clique-degree exceeds 2^32 - 1";
     default: return "unknown status";
   }
 }
@@ -30,6 +31,7 @@ extern "C" int nh_version(void) { return 100; }
 // fault injection (include/nucleus_debug.h); read by the drivers in nh_peel.cu and nh_orient.cu
 long long g_nh_inject_wait_ns = 0;
 long long g_nh_inject_table_cap = 0;
+long long g_nh_inject_count_base = 0;
 
 extern "C" int nh_debug_inject(int what, int64_t value) {
   if (value < 0) return NH_ERR_INVALID;
@@ -40,6 +42,11 @@ extern "C" int nh_debug_inject(int what, int64_t value) {
   if (what == NH_INJECT_TABLE_CAP) {
     if (value != 0 && (value & (value - 1))) return NH_ERR_INVALID;
     g_nh_inject_table_cap = (long long)value;
+    return NH_OK;
+  }
+  if (what == NH_INJECT_COUNT_BASE) {
+    if (value > 0xffffffffll) return NH_ERR_INVALID;
+    g_nh_inject_count_base = (long long)value;
     return NH_OK;
   }
   return NH_ERR_INVALID;

@@ -3,6 +3,8 @@
 // out-lists; the s-clique-degree of each of its binom(s,r) r-subsets is incremented.
 #include "nh_internal.cuh"
 
+extern long long g_nh_inject_count_base;  // fault injection (nh_api.cu): initial count value
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -14,11 +16,17 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
   return v;
 }
 
+// cnt[x] += inc with a check that the uint32 count does not wrap (status NH_ERR_COUNT_OVERFLOW)
+__device__ __forceinline__ void cnt_add(uint32_t* cnt, int64_t x, uint32_t inc, int* status) {
+  const uint32_t old = atomicAdd(&cnt[x], inc);
+  if (old > 0xffffffffu - inc) atomicCAS(status, 0, NH_ERR_COUNT_OVERFLOW);
+}
+
 __device__ __forceinline__ void tri_add(const GView& g, unsigned long long key, uint32_t inc, uint32_t* cnt,
                                         int* status) {
   int64_t id = nh_tri_lookup(g.table, g.mask, key);
   if (id < 0) { atomicExch(status, NH_ERR_INTERNAL); return; }
-  atomicAdd(&cnt[id], inc);
+  cnt_add(cnt, id, inc, status);
 }
 
 // (1,2): the s-clique-degree of a vertex is its degree
@@ -65,7 +73,7 @@ struct ItemCursor {
 template <int R>
 __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ n_s,
                            const int32_t* __restrict__ order, unsigned long long* __restrict__ next,
-                           float* __restrict__ cost) {
+                           float* __restrict__ cost, int* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -87,13 +95,13 @@ __global__ void k_count_s3(GView g, uint32_t* __restrict__ cnt, unsigned long lo
       if (q < 0) continue;
       tot++;
       const int32_t e_vb = g.oeid[scan_v ? j : q], e_ab = g.oeid[scan_v ? q : j];
-      if (R == 1) atomicAdd(&cnt[b], 1u);
-      if (R == 2) { atomicAdd(&cnt[e_vb], 1u); atomicAdd(&cnt[e_ab], 1u); }
+      if (R == 1) cnt_add(cnt, b, 1u, status);
+      if (R == 2) { cnt_add(cnt, e_vb, 1u, status); cnt_add(cnt, e_ab, 1u, status); }
     }
     tot = warp_sum(tot);
     if (lane == 0 && tot) {
-      if (R == 1) { atomicAdd(&cnt[v], tot); atomicAdd(&cnt[a], tot); }
-      if (R == 2) atomicAdd(&cnt[e_va], tot);
+      if (R == 1) { cnt_add(cnt, v, tot, status); cnt_add(cnt, a, tot, status); }
+      if (R == 2) cnt_add(cnt, e_va, tot, status);
       found += tot;
     }
     if (cost && lane == 0) atomicAdd(&cost[v], (float)(se - sb) * (1.0f + log2p1(le - lb)) + 1.0f);
@@ -166,8 +174,8 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
         if (k < 0) continue;
         n3++;
         const int32_t e_vc = c2e1[k], e_ac = c2e2[k], e_bc = g.oeid[j];
-        if (R == 1) atomicAdd(&cnt[c], 1u);
-        if (R == 2) { atomicAdd(&cnt[e_vc], 1u); atomicAdd(&cnt[e_ac], 1u); atomicAdd(&cnt[e_bc], 1u); }
+        if (R == 1) cnt_add(cnt, c, 1u, status);
+        if (R == 2) { cnt_add(cnt, e_vc, 1u, status); cnt_add(cnt, e_ac, 1u, status); cnt_add(cnt, e_bc, 1u, status); }
         if (R == 3) {
           tri_add(g, nh_tri_key(v, a, c, e_va, e_vc, e_ac), 1u, cnt, status);
           tri_add(g, nh_tri_key(v, b, c, e_vb, e_vc, e_bc), 1u, cnt, status);
@@ -176,15 +184,15 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
       }
       n3 = warp_sum(n3);
       if (lane == 0 && n3) {
-        if (R == 1) atomicAdd(&cnt[b], n3);
-        if (R == 2) { atomicAdd(&cnt[e_vb], n3); atomicAdd(&cnt[e_ab], n3); }
+        if (R == 1) cnt_add(cnt, b, n3, status);
+        if (R == 2) { cnt_add(cnt, e_vb, n3, status); cnt_add(cnt, e_ab, n3, status); }
         if (R == 3) tri_add(g, nh_tri_key(v, a, b, e_va, e_vb, e_ab), n3, cnt, status);
       }
       tot_item += n3;
     }
     if (lane == 0 && tot_item) {
-      if (R == 1) { atomicAdd(&cnt[v], tot_item); atomicAdd(&cnt[a], tot_item); }
-      if (R == 2) atomicAdd(&cnt[e_va], tot_item);
+      if (R == 1) { cnt_add(cnt, v, tot_item, status); cnt_add(cnt, a, tot_item, status); }
+      if (R == 2) cnt_add(cnt, e_va, tot_item, status);
       found += tot_item;
     }
     if (cost && lane == 0) atomicAdd(&cost[v], work);
@@ -203,6 +211,10 @@ int grid_for(const void* fn, int threads, size_t smem) {
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+__global__ void k_fill_u32(int64_t n, uint32_t* __restrict__ a, uint32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
+}
 
 }  // namespace
 
@@ -227,13 +239,18 @@ int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t*
   unsigned long long* next = nullptr;
   int rc = NH_OK;
   if (measure) cudaMemsetAsync(measure, 0, sizeof(float) * (size_t)o->n, st);
-  cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ri->n_r, st);
+  if (g_nh_inject_count_base == 0) {
+    cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)ri->n_r, st);
+  } else {  // fault injection: counts start near 2^32 (tests of the overflow check)
+    k_fill_u32<<<nh_blocks_for(ri->n_r, 256, 152 * 32), 256, 0, st>>>(ri->n_r, cnt, (uint32_t)g_nh_inject_count_base);
+    nh_note_launch();
+  }
   if (s == 3) {
     const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
     int grid = grid_for(fn, kThreads, 0);
     if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) return rc;
-    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
-    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure);
+    if (r == 1) k_count_s3<1><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure, status);
+    else k_count_s3<2><<<grid, kThreads, 0, st>>>(g, cnt, dcount, order, next, measure, status);
     nh_note_launch();
   } else {
     const int cap = (int)(o->max_out > 0 ? o->max_out : 1);

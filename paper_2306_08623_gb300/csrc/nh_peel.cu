@@ -77,7 +77,7 @@ __global__ void k_max_u32(int64_t n, const uint32_t* __restrict__ a, unsigned in
 
 // nh_link_pairs: one thread per call
 __global__ void k_link_pairs(LinkEnv E, const int2* __restrict__ pairs, unsigned long long n) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const int2 p = pairs[i];
@@ -94,7 +94,7 @@ __global__ void k_link_swap(PeelCtl* c, unsigned long long cap) {
 }
 
 __global__ void k_link_drain(LinkEnv E) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const unsigned int b = E.ctl->drain_buf;
   const unsigned long long n = E.ctl->drain_n;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;

@@ -99,7 +99,7 @@ struct PeelArgs {
 };
 
 struct LocalStats {
-  unsigned long long listed, dec, link, unite, scan, probe, ovf, stamp;
+  unsigned long long listed, dec, link, unite, scan, probe, ovf, stamp, expand;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -334,7 +334,7 @@ __device__ __forceinline__ void add_delta(LocalStats& ls, const LinkDelta& d) {
 }
 
 static __device__ __noinline__ LinkDelta link_run_call(const LinkEnv E, int32_t R0, int32_t Q0) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   link_run(E, R0, Q0, ls);
   return LinkDelta{ls.link, ls.unite, ls.ovf};
 }
@@ -417,7 +417,7 @@ __device__ __forceinline__ void wl_add(const WarpLinks& W, const PeelArgs& A, in
 // registers
 static __device__ __noinline__ LinkDelta wl_flush_impl(const WarpLinks W, const LinkEnv E, const uint32_t* val,
                                                        int32_t Rid, int lane) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   __syncwarp();
   const int n = min(*(volatile int*)W.cnt, kLinkBuf);
   if (n == 0) return LinkDelta{0, 0, 0};
@@ -479,6 +479,7 @@ __device__ __forceinline__ void wl_maybe_flush(const WarpLinks& W, const PeelArg
 template <int CM, bool EXACT>
 __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM], uint32_t t,
                                           uint32_t thr, int32_t* nf, const WarpLinks& W, LocalStats& ls) {
+  ls.stamp += CM;
   if (A.union_mode) {
     // two-phase hierarchy at level thr (= core of Rid): an s-clique whose least member core is
     // thr joins all its members; its member of least id among those of core thr does it
@@ -655,6 +656,7 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
             mem[i] = __ldg(g.ettid + j);
           } else if (ok) {
             const int64_t p = nh_find(g.etw, tl[i], th[i], w);
+            ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps and the id
             if (p < 0) ok = false;
             else mem[i] = __ldg(g.ettid + p);
           }
@@ -706,6 +708,7 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
           ew[i] = __ldg(g.eid + j);
         } else if (ok) {
           const int64_t id = nh_edge_id(g, vx[i], w);  // one probe instead of a binary search
+          ls.scan += 3;                               // an 8-byte key and a 4-byte id
           if (id < 0) ok = false;
           else ew[i] = (int32_t)id;
         }
@@ -756,12 +759,14 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
           const int64_t q = __ldg(g.ooff + ow) + (int64_t)(idx - (oincl - olen));
           const int32_t x = __ldg(g.oadj + q);
           const int32_t e_wx = __ldg(g.oeid + q);
+          ls.scan += 2;
           bool okx = true;
           int32_t ex[2] = {0, 0};
 #pragma unroll
           for (int i = 0; i < R; i++) {
             if (!okx) break;
             const int64_t id = nh_edge_id(g, vx[i], x);
+            ls.scan += 3;
             if (id < 0) okx = false;
             else ex[i] = (int32_t)id;
           }
@@ -1003,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
   const int lane = threadIdx.x & 31;
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   extern __shared__ __align__(16) unsigned char s_dyn[];
   unsigned long long* s_links = reinterpret_cast<unsigned long long*>(s_dyn + kSmLinks);
   uint32_t* s_pref = reinterpret_cast<uint32_t*>(s_dyn + kSmPref);
@@ -1170,7 +1175,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(Peel
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   extern __shared__ __align__(16) unsigned char s_dyn[];
   unsigned long long* s_links = reinterpret_cast<unsigned long long*>(s_dyn + kSmLinks);
   uint32_t* s_pref = reinterpret_cast<uint32_t*>(s_dyn + kSmPref);

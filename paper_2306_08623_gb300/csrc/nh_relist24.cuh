@@ -310,7 +310,7 @@ __device__ __forceinline__ void c24_pair(const PeelArgs& A, int32_t Rid, uint32_
   const int32_t x = __ldg(A.g.oadj + q);
   const int32_t eq = __ldg(A.g.oeid + q);
   ls.scan += 2;
-  ls.probe++;
+  ls.expand++;
   const int px = c24_find(G, x);
   if (px < 0) return;
   e = eq;
@@ -673,7 +673,7 @@ __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long 
   const C24Area Gb = c24_area(smem, kC24BlockHS, 12, kC24BlockCap);
   const bool split = n <= (unsigned long long)kTaskItems;
   const unsigned long long ntask = c24_prefix(A, items, n, nwarps, s_pref, s_red);
-  const unsigned long long probe0 = ls.probe;
+  const unsigned long long expand0 = ls.expand;
   if (A.round_log && blockIdx.x == 0 && threadIdx.x == 0) ctl->c24_tasks = ntask;
   // warps: sub-tasks in batches from a shared counter
   const unsigned long long per = ntask / ((unsigned long long)nwarps * 8ull);
@@ -729,7 +729,7 @@ __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long 
                           wacc, tcnt + 8, wcnt, s_red, ls);
   }
   if (A.round_log) {
-    const unsigned long long d = warp_sum_u64(ls.probe - probe0);
+    const unsigned long long d = warp_sum_u64(ls.expand - expand0);
     if (lane == 0 && d) atomicAdd(&ctl->dbg_work, d);
   }
 }

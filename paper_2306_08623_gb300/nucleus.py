@@ -258,6 +258,18 @@ def hierarchy_enqueue(o: Oriented, ri: RIndex, s: int, buf: dict, stream=None):
         _dptr(buf["L"]), _dptr(buf["parent"]), _dptr(buf["label"]), _dptr(buf["res"]), _stream(stream)))
 
 
+def capture_hierarchy(o: Oriented, ri: RIndex, s: int, buf: dict):
+    """hierarchy_enqueue captured into a CUDA graph (after one eager warm-up call): replaying the
+    returned torch.cuda.CUDAGraph reruns counts, peel and construct-tree into buf."""
+    hierarchy_enqueue(o, ri, s, buf)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+        hierarchy_enqueue(o, ri, s, buf)
+    return g
+
+
 def construct_tree_noalloc(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent: torch.Tensor,
                            label: torch.Tensor, stream=None):
     """nh_construct_tree without device allocation (n_r <= TREE_NOALLOC_MAX): the outputs are the
@@ -461,10 +473,11 @@ def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: s
     """The whole exact path on device tensors: orientation, r-clique index, s-clique counts, peel
     and hierarchy.  method "el": link-efficient interleaved with the peel, then construct-tree
     (Alg. 3 + Alg. 5); "te": core numbers, then the two-phase hierarchy (§7.4, definitional
-    reading only); "auto": "el" for s - r = 1 and "te" otherwise (the paper's finding that the
-    two-phase form wins as s - r grows)."""
+    reading only); "auto": the builder measured faster on a GB300 (R-MAT 18, peel + hierarchy):
+    "te" for every pair but (3,4), whose linking peel is faster than its cores-only peel plus the
+    two-phase hierarchy; "el" for the pair rule (link_mode "pair"), which only "el" follows."""
     if method == "auto":
-        method = "el" if s - r == 1 or link_mode != "def" else "te"
+        method = "el" if (r, s) == (3, 4) or link_mode != "def" else "te"
     o = build_orientation(off, adj, stream)
     ri = index_r_cliques(o, r, stream)
     cnt, n_s = count_s_cliques(o, ri, s, stream=stream)

@@ -67,3 +67,8 @@ def test_debug_injection_validates_its_arguments():
     assert lib.nh_debug_inject(2, 48) == 1   # not a power of two
     assert lib.nh_debug_inject(1, -5) == 1
     assert lib.nh_debug_inject(9, 1) == 1
+    assert lib.nh_debug_inject(3, (1 << 32) - 3) == 0
+    assert lib.nh_debug_inject(3, 1 << 32) == 1  # beyond uint32
+    assert lib.nh_debug_inject(3, 0) == 0
+    lib.nh_status_string.restype = ctypes.c_char_p
+    assert b"2^32" in lib.nh_status_string(9)

@@ -15,8 +15,8 @@ from helpers import compare_hierarchy, u32  # noqa: E402
 from paper_2306_08623_gb300 import graphgen as gg  # noqa: E402
 
 pytestmark = pytest.mark.gpu
-NH_INJECT_WAIT_NS, NH_INJECT_TABLE_CAP = 1, 2
-NH_ERR_TABLE_FULL, NH_ERR_TIMEOUT = 3, 5
+NH_INJECT_WAIT_NS, NH_INJECT_TABLE_CAP, NH_INJECT_COUNT_BASE = 1, 2, 3
+NH_ERR_TABLE_FULL, NH_ERR_TIMEOUT, NH_ERR_COUNT_OVERFLOW = 3, 5, 9
 
 
 @pytest.fixture(scope="module")
@@ -30,6 +30,7 @@ def nc():
     yield mod
     lib.nh_debug_inject(NH_INJECT_WAIT_NS, 0)
     lib.nh_debug_inject(NH_INJECT_TABLE_CAP, 0)
+    lib.nh_debug_inject(NH_INJECT_COUNT_BASE, 0)
 
 
 def _inject(nc, what, value):
@@ -88,3 +89,27 @@ def test_small_tables_report_table_full(nc):
     finally:
         _inject(nc, NH_INJECT_TABLE_CAP, 0)
     _normal_run_matches_oracle(nc, off, adj, 3, 4)
+
+
+@pytest.mark.parametrize("r,s", [(1, 3), (2, 3), (2, 4), (3, 4)])
+def test_count_overflow_is_reported(nc, r, s):
+    """Every r-clique of K_7 lies in C(7-r, s-r) >= 3 s-cliques: counts that start at 2^32 - 3
+    wrap and counting reports NH_ERR_COUNT_OVERFLOW; started at 2^32 - 100 they end at the
+    start plus the s-clique-degree, with no error."""
+    from math import comb
+    off, adj = gg.complete(7)
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    o = nc.build_orientation(d_off, d_adj)
+    ri = nc.index_r_cliques(o, r)
+    try:
+        _inject(nc, NH_INJECT_COUNT_BASE, (1 << 32) - 3)
+        with pytest.raises(nc.NucleusError) as e:
+            nc.count_s_cliques(o, ri, s)
+        assert e.value.status == NH_ERR_COUNT_OVERFLOW
+        _inject(nc, NH_INJECT_COUNT_BASE, (1 << 32) - 100)
+        cnt, n_s = nc.count_s_cliques(o, ri, s)
+        assert n_s == comb(7, s)
+        assert (u32(cnt).astype(np.int64) == (1 << 32) - 100 + comb(7 - r, s - r)).all()
+    finally:
+        _inject(nc, NH_INJECT_COUNT_BASE, 0)
+    _normal_run_matches_oracle(nc, off, adj, r, s)

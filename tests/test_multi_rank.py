@@ -45,15 +45,21 @@ def test_single_rank_is_unchanged():
 
 
 def test_pair_report_arithmetic():
-    """The bench's per-pair figures from a step's counters (CPU, no GPU)."""
+    """The bench's per-pair figures from a step's counters (CPU, no GPU): the algorithmic bytes
+    follow B = 4 E_scan + 8 U_cnt + 16 P_hash + 8 N_link + 12 frontier + 4 stamp reads."""
     import bench as b
-    stats = {"rounds": 7, "scan_elements": 100, "s_cliques_listed": 50, "decrements": 20, "hash_probes": 0,
-             "link_calls": 10, "frontier_total": 40}
+    stats = {"rounds": 7, "scan_elements": 100, "s_cliques_listed": 50, "decrements": 20, "hash_probes": 3,
+             "link_calls": 10, "frontier_total": 40, "stamp_reads": 60}
     info = {(2, 3): {"n_r": 40, "n_s": 30, "n_nodes": 3, "stats": stats}}
-    rep = b.pair_report(info, {(2, 3): 2.0}, {(2, 3): 1.0}, {(2, 3): 5.0}, 1000.0)["2,3"]
-    alg = 4 * 100 + 4 * 2 * 50 + 8 * 20 + 8 * 10 + 12 * 40  # C(3,2) = 3 members, 2 others
-    assert b.algorithmic_peel_bytes(stats, 2, 3) == alg
+    oracle_res = {"2,3": {"n_s": 30, "seconds": 0.6, "core_equal": True}}
+    rep = b.pair_report(info, {(2, 3): 2.0}, {(2, 3): 1.0}, {(2, 3): 5.0}, 1000.0, oracle_res)["2,3"]
+    alg = 4 * 100 + 8 * 20 + 16 * 3 + 8 * 10 + 12 * 40 + 4 * 60
+    assert b.algorithmic_peel_bytes(stats) == alg
     assert rep["s_cliques_peeled_per_s"] == 30 / 0.002
     assert abs(rep["peel_algorithmic_gbs"] - round(alg / 0.002 / 1e9, 3)) < 1e-12
     assert rep["method"] == b.METHOD[(2, 3)]
     assert rep["peel_frac_of_hbm_peak"] == (alg / 0.002 / 1e9) / 1000.0
+    assert rep["oracle_seconds"] == 0.6 and rep["gpu_peel_and_hierarchy_vs_oracle"] == 0.6 / 0.003
+    assert rep["oracle_core_equal"] is True
+    rep4 = b.pair_report({(2, 4): info[(2, 3)]}, {(2, 4): 2.0}, {(2, 4): 1.0}, {}, 1000.0, oracle_res)["2,4"]
+    assert "not run" in rep4["oracle_seconds"]
