@@ -46,7 +46,10 @@ __device__ __forceinline__ float log2p1(int64_t x) { return log2f((float)x + 1.0
 
 constexpr unsigned long long kChunk = 8;
 
-// next work item of this warp, or -1 when there is none left (warp-uniform)
+// next work item of this warp, or -1 when there is none left (warp-uniform).  Dynamic chunks grow
+// with the position in the order: the items come heaviest first, so the first grabs take kChunk
+// items and later ones about (position / (16 * warps)) of the lighter items, which keeps the
+// shared counter to a few dozen grabs per warp.
 struct ItemCursor {
   const int32_t* order;
   unsigned long long* next;
@@ -59,12 +62,14 @@ struct ItemCursor {
       return q < m ? q : -1;
     }
     if (cur >= end) {
+      unsigned long long want = end / (16ull * (unsigned long long)nwarps);
+      if (want < kChunk) want = kChunk;
       unsigned long long b = 0;
-      if (lane == 0) b = atomicAdd(next, kChunk);
+      if (lane == 0) b = atomicAdd(next, want);
       b = __shfl_sync(NH_FULL, b, 0);
       if (b >= (unsigned long long)m) return -1;
       cur = b;
-      end = min(b + kChunk, (unsigned long long)m);
+      end = min(b + want, (unsigned long long)m);
     }
     return order[cur++];
   }

@@ -75,8 +75,13 @@ __global__ void k_degree_cost(GView g, int s, float* __restrict__ cost) {
 
 // per out-edge item: its source vertex's cost spread evenly over the vertex's out-edges; the item's
 // bucket is 31 - floor(log2(cost + 1)), so bucket 0 holds the heaviest items
+// per item: its cost bucket (31 - floor(log2(cost per out-entry + 1))); per-bucket counts are
+// summed in shared memory and added once per block
 __global__ void k_item_bucket(GView g, const float* __restrict__ vcost, uint8_t* __restrict__ bucket,
                               uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[32];
+  if (threadIdx.x < 32) sh[threadIdx.x] = 0;
+  __syncthreads();
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.m; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = g.osrc[p];
     const float d = (float)(g.ooff[v + 1] - g.ooff[v]);
@@ -84,15 +89,34 @@ __global__ void k_item_bucket(GView g, const float* __restrict__ vcost, uint8_t*
     const int lg = (int)fminf(floorf(log2f(c + 1.0f)), 31.0f);
     const uint8_t bk = (uint8_t)(31 - lg);
     bucket[p] = bk;
-    atomicAdd(hist + bk, 1u);
+    atomicAdd(sh + bk, 1u);
   }
+  __syncthreads();
+  if (threadIdx.x < 32 && sh[threadIdx.x]) atomicAdd(hist + threadIdx.x, sh[threadIdx.x]);
 }
 
+// items in bucket order: every block takes one contiguous range of items, counts it per bucket
+// in shared memory, reserves each bucket's share with one atomic per bucket and writes its items
+// there (the order inside a bucket does not matter)
 __global__ void k_item_scatter(int64_t m, const uint8_t* __restrict__ bucket, const int64_t* __restrict__ off,
                                unsigned long long* __restrict__ cursor, int32_t* __restrict__ order) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+  __shared__ uint32_t cnt[32];
+  __shared__ unsigned long long base[32];
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * per;
+  const int64_t b1 = b0 + per < m ? b0 + per : m;
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) atomicAdd(cnt + bucket[p], 1u);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(cursor + threadIdx.x, (unsigned long long)cnt[threadIdx.x]) : 0ull;
+    cnt[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
     const uint8_t bk = bucket[p];
-    order[off[bk] + (int64_t)atomicAdd(cursor + bk, 1ull)] = (int32_t)p;
+    order[off[bk] + (int64_t)(base[bk] + atomicAdd(cnt + bk, 1u))] = (int32_t)p;
   }
 }
 

@@ -553,6 +553,24 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 // re-listing of one frontier r-clique by one warp
 // ---------------------------------------------------------------------------------------------
 
+// Whether an s-clique with member x (besides R) can still be one R handles: always for the
+// linking peels (a dead s-clique is linked too); otherwise not when x was peeled in an earlier
+// round or is in the frontier with a smaller id (peel), or when x lies below the level or is of
+// the level with a smaller id (two-phase hierarchy; the label hierarchy keeps the latter, whose
+// s-cliques still mark R).  process_S decides exactly; this only saves the searches for the rest.
+__device__ __forceinline__ bool member_may_count(const PeelArgs& A, int32_t Rid, int32_t x, uint32_t t, uint32_t thr,
+                                                 LocalStats& ls) {
+  if (A.union_mode) {
+    const uint32_t c = __ldcg(A.val + x);
+    ls.stamp++;
+    return c >= thr && (A.mark || c > thr || x > Rid);
+  }
+  if (A.link_mode == 0 || A.link_mode == 1) return true;
+  const uint32_t rd = __ldcg(A.round + x);
+  ls.stamp++;
+  return !((rd != 0u && rd < t) || (rd == t && x < Rid));
+}
+
 // Length of the list whose 32-entry chunks the re-listing of r-clique Rid walks: the adjacency
 // list of its vertex of least degree, for (2,3) with per-edge triangle lists the edge's own list,
 // or for (3,4) the shortest triangle list of its three edges.
@@ -650,11 +668,13 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
       int32_t mem[3] = {0, 0, 0};
       if (ok) {
         const int32_t w = __ldg(g.etw + j);
+        mem[bt] = __ldg(g.ettid + j);
+        // without links, an s-clique whose member from the scanned list is dead, below the level
+        // or another frontier member's is none of R's business: skip the two searches
+        ok = member_may_count(A, Rid, mem[bt], t, thr, ls);
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-          if (i == bt) {
-            mem[i] = __ldg(g.ettid + j);
-          } else if (ok) {
+          if (i != bt && ok) {
             const int64_t p = nh_find(g.etw, tl[i], th[i], w);
             ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps and the id
             if (p < 0) ok = false;
@@ -832,7 +852,8 @@ __device__ __forceinline__ bool relist_prefix(const PeelArgs& A, const int32_t* 
 }
 
 // Re-lists the n r-cliques of items: in tasks (see relist_prefix) when `tasks`, else with G warps
-// per r-clique (G, a power of two up to gmax, as many as the grid has for the list; for s - r = 2
+// per r-clique (G, a power of two up to gmax, as many as the grid has for the list; G = 1: warps
+// take r-cliques in batches from a shared counter; for s - r = 2
 // the G warps form G / Ge chunk-groups of Ge warps, the Ge warps of one chunk-group scanning the
 // same 32 candidates and each expanding the out-lists of every Ge-th of them).  One call site of
 // relist_item per kernel.
@@ -856,6 +877,11 @@ __device__ __forceinline__ void relist_list(const PeelArgs& A, const int32_t* it
   const long long ngroups = nwarps / G, grp = gwarp / G;
   const int sub = (int)(gwarp % G), Gc = G / Ge, sc = sub / Ge, se_g = sub % Ge;
   unsigned long long it = (unsigned long long)grp;
+  // one warp per r-clique: r-cliques in batches from the shared counter (per-r-clique work is
+  // heavy-tailed, so a fixed stride would leave the round to its unluckiest warp)
+  const unsigned long long dper = n / ((unsigned long long)nwarps * 16ull);
+  const unsigned long long dbt = dper > 0 ? dper : 1ull;
+  unsigned long long dk = 0, dk1 = 0;
   int32_t curR = -1;
   for (;;) {
     int32_t Rid;
@@ -887,6 +913,22 @@ __device__ __forceinline__ void relist_list(const PeelArgs& A, const int32_t* it
       ge = Ge_t;
       se = (int)(k % (unsigned long long)Ge_t);
       k += run;
+    } else if (G == 1) {
+      if (dk >= dk1) {
+        unsigned long long k0 = 0;
+        if (lane == 0) k0 = atomicAdd(task_next, dbt);
+        k0 = __shfl_sync(NH_FULL, k0, 0);
+        if (k0 >= n) break;
+        dk = k0;
+        dk1 = k0 + dbt < n ? k0 + dbt : n;
+      }
+      Rid = __ldcg(items + dk);
+      ++dk;
+      c0 = 0;
+      cstep = 1;
+      cend = INT64_MAX;
+      ge = 1;
+      se = 0;
     } else {
       if (grp >= ngroups || it >= n) break;
       Rid = __ldcg(items + it);
