@@ -16,6 +16,9 @@ Parity status per function:
   * ``nucleus(..., approx_delta=d)`` Alg. 2 -- pinned by Thm. 2's bound, lower bound,
     special cases (K_n, huge delta, disjoint cliques) and a hand-worked example.
   * ``check_sample`` local certificate -- pinned by planting mistakes into oracle output.
+  * ``certify`` local certificate over every r-clique and s-clique (certify.c), for full-size
+    checks -- pinned against ``nucleus`` on random graphs (zero violations), against
+    ``check_sample`` over all r-cliques, and by planting each kind of mistake.
 """
 from __future__ import annotations
 
@@ -28,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nucleus_oracle.c")
+_SRC_CERT = os.path.join(_HERE, "certify.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 HIER_MODES = {None: 0, "def": 1, "pair": 2, "link_def": 3, "link_pair": 4}
@@ -36,9 +40,11 @@ HIER_MODES = {None: 0, "def": 1, "pair": 2, "link_def": 3, "link_pair": 4}
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler into oracle/_build/liboracle.so."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in (_SRC, _SRC_CERT))
+    if force or stale:
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_CERT,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +67,7 @@ class _Result(ctypes.Structure):
         ("approx_T", ctypes.c_uint32),
         ("n_thresholds", ctypes.c_int32),
         ("thresholds", ctypes.POINTER(ctypes.c_uint32)),
+        ("removal", ctypes.POINTER(ctypes.c_uint32)),
     ]
 
 
@@ -92,6 +99,9 @@ def _load():
         lib.orc_approx_thresholds.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_uint32, P, ctypes.c_int]
         lib.orc_approx_round_cap.restype = ctypes.c_uint32
         lib.orc_approx_round_cap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64]
+        lib.crt_certify.restype = ctypes.c_int
+        lib.crt_certify.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, P, P, P, P, P,
+                                    ctypes.c_int64, ctypes.c_int, P]
         lib.orc_check_sample.restype = ctypes.c_int
         lib.orc_check_sample.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64,
                                          P, ctypes.c_int64, P, P, P, P, P, P]
@@ -130,7 +140,8 @@ def nucleus(off, adj, r: int, s: int, core: bool = True, hier: str | None = "def
             approx_delta: float | None = None) -> dict:
     """Run the oracle.  Returns a dict with (as present):
     n_r, n_s, tuples (n_r, r), cnt, core, kmax, leaf_node, node_parent, node_label,
-    n_link_calls, n_unite_calls, approx, approx_rounds, approx_T, thresholds."""
+    n_link_calls, n_unite_calls, approx, approx_rounds, approx_T, thresholds, removal (1-based
+    position of each r-clique in the exact peel's removal order)."""
     off, adj = _csr(off, adj)
     lib = _load()
     flags = (1 if core else 0) | (2 if approx_delta is not None else 0)
@@ -149,6 +160,8 @@ def nucleus(off, adj, r: int, s: int, core: bool = True, hier: str | None = "def
         if res.core:
             out["core"] = _copy(res.core, n_r, np.uint32)
             out["kmax"] = int(res.kmax)
+        if res.removal:
+            out["removal"] = _copy(res.removal, n_r, np.uint32)
         if hier is not None:
             nn = res.n_nodes
             out["n_nodes"] = nn
@@ -286,6 +299,29 @@ def check_sample(off, adj, r: int, s: int, tuples, sample, cnt=None, core=None, 
     if rc != 0:
         raise RuntimeError("check_sample failed with status %d" % rc)
     return bad
+
+
+def certify(off, adj, r: int, s: int, n_r: int, cnt=None, core=None, rnd=None, parent=None, label=None,
+            n_nodes: int = 0, threads: int | None = None) -> dict:
+    """Local certificate of a claimed exact decomposition over EVERY r-clique and s-clique
+    (certify.c): count, validity and peel-order conditions (which prove the core numbers) and the
+    hierarchy's under- and over-merge conditions (which prove it equals the definitional one).
+    Returns the number of violations of each, whether the hierarchy was checked (trees up to
+    16384 nodes with parents below their children's labels), and the s-cliques enumerated."""
+    off, adj = _csr(off, adj)
+    lib = _load()
+    conv = lambda a, dt: None if a is None else np.ascontiguousarray(a, dtype=dt)
+    cnt, core, rnd = conv(cnt, np.uint32), conv(core, np.uint32), conv(rnd, np.uint32)
+    parent, label = conv(parent, np.int32), conv(label, np.uint32)
+    out = np.zeros(8, dtype=np.int64)
+    threads = threads or min(16, os.cpu_count() or 1)
+    rc = lib.crt_certify(len(off) - 1, _ptr(off), _ptr(adj), r, s, int(n_r), _ptr(cnt), _ptr(core), _ptr(rnd),
+                         _ptr(parent), _ptr(label), int(n_nodes), int(threads), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("certify failed with status %d" % rc)
+    return {"count": int(out[0]), "validity": int(out[1]), "peel_order": int(out[2]),
+            "under_merge": int(out[3]), "over_merge": int(out[4]), "hierarchy_checked": bool(out[5]),
+            "n_s": int(out[6]), "single_part_nodes": int(out[7])}
 
 
 def binom(s: int, r: int) -> int:

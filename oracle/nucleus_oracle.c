@@ -218,13 +218,14 @@ typedef struct {
   uint32_t approx_T;
   int32_t n_thresholds;
   uint32_t* thresholds;   /* [n_thresholds]                                                */
+  uint32_t* removal;      /* [n_r] 1-based position in the exact peel's removal order, or NULL */
 } orc_result;
 
 void orc_free(orc_result* res) {
   if (!res) return;
   free(res->tuples); free(res->cnt); free(res->core);
   free(res->leaf_node); free(res->node_parent); free(res->node_label);
-  free(res->approx); free(res->thresholds);
+  free(res->approx); free(res->thresholds); free(res->removal);
   free(res);
 }
 
@@ -237,7 +238,8 @@ void orc_free(orc_result* res) {
  * other member whose degree is above the removed one's loses 1 (a member already at that level
  * stays there: the running maximum makes its core that level anyway). */
 static int exact_peel(int64_t n_r, const uint32_t* cnt0, const int64_t* inc_off, const int64_t* inc,
-                      const int32_t* members, int C, int64_t n_s, uint32_t* core, uint32_t* kmax_out) {
+                      const int32_t* members, int C, int64_t n_s, uint32_t* core, uint32_t* kmax_out,
+                      uint32_t* removal) {
   uint32_t md = 0;
   for (int64_t i = 0; i < n_r; i++) if (cnt0[i] > md) md = cnt0[i];
   uint32_t* d = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
@@ -259,6 +261,7 @@ static int exact_peel(int64_t n_r, const uint32_t* cnt0, const int64_t* inc_off,
   for (int64_t i = 0; i < n_r; i++) {
     int64_t R = vert[i];
     core[R] = d[R];
+    if (removal) removal[R] = (uint32_t)(i + 1);
     if (d[R] > kmax) kmax = d[R];
     for (int64_t q = inc_off[R]; q < inc_off[R + 1]; q++) {
       int64_t S = inc[q];
@@ -749,7 +752,10 @@ static orc_result* nucleus_impl(int64_t n, const int64_t* off, const int32_t* ad
   } else if ((flags & ORC_WANT_CORE) || hier_mode != ORC_HIER_NONE) {
     res->core = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
     if (!res->core) { res->status = ORC_ERR_NOMEM; goto done; }
-    res->status = exact_peel(n_r, res->cnt, inc_off, inc, mc.members, C, n_s, res->core, &res->kmax);
+    res->removal = malloc(sizeof(uint32_t) * (n_r ? n_r : 1));
+    if (!res->removal) { res->status = ORC_ERR_NOMEM; goto done; }
+    res->status = exact_peel(n_r, res->cnt, inc_off, inc, mc.members, C, n_s, res->core, &res->kmax,
+                             res->removal);
     if (res->status) goto done;
   }
   if (hier_mode == ORC_HIER_DEF || hier_mode == ORC_HIER_PAIR) {

@@ -1,13 +1,18 @@
 """Parity at the benchmark's full size: R-MAT scale 18, edge factor 16, seed 2, in the launch
 configuration bench.py times.
 
-(1,2) and (2,3): element-wise against the oracle (counts, core numbers, hierarchy).
-(2,4) and (3,4): the oracle cannot enumerate 2.3e9 4-cliques in test time, so sampled r-cliques
-are checked one by one with the oracle's local certificate (count from the definition; at least
-core[R] s-cliques inside the set of core >= core[R]; at most core[R] live s-cliques when peeled;
-every sampled s-clique's members meet in one hierarchy node at level c_S), plus properties that
-hold at any size.  Approximate core numbers: Thm. 2's bound for every r-clique.
+(1,2) and (2,3): element-wise against the oracle (counts, core numbers, hierarchy) for both
+hierarchy builders, and the approximate (2,3) values bit-exact against the oracle for delta 0.1
+and 0.5.  The oracle runs in spawned host processes started with the module, beside the GPU work.
+(2,4) and (3,4): the oracle cannot enumerate 2.3e9 4-cliques in test time; every r-clique and
+every s-clique is checked with the oracle's full local certificate (oracle.certify: counts,
+validity and peel order, which prove the core numbers; under- and over-merge, which prove the
+hierarchy), for the hierarchy builders the benchmark uses ((2,4) two-phase, (3,4) linking peel)
+and the other one for (3,4); plus properties that hold at any size.  Approximate (3,4) values:
+Thm. 2's bound for every r-clique.
 """
+import multiprocessing as mp
+import os
 from math import comb
 
 import numpy as np
@@ -22,6 +27,34 @@ from paper_2306_08623_gb300 import graphgen as gg  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
+def _oracle_job(job):
+    """(kind, r, s, delta) -> the oracle's result on R-MAT 18 EF16 seed 2 (runs in a spawned process)."""
+    import oracle as orc
+    from paper_2306_08623_gb300 import graphgen as g
+    kind, r, s, delta = job
+    off, adj = g.rmat(18, 16, 2)
+    if kind == "exact":
+        return orc.nucleus(off, adj, r, s, hier="def")
+    res = orc.nucleus(off, adj, r, s, hier=None, approx_delta=delta)
+    return {"approx": res["approx"], "approx_rounds": res["approx_rounds"]}
+
+
+JOBS = [("exact", 1, 2, None), ("exact", 2, 3, None), ("approx", 2, 3, 0.1), ("approx", 2, 3, 0.5)]
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    """The oracle's full-size results, computed in parallel host processes; a dict of futures."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    pool = mp.get_context("spawn").Pool(processes=len(JOBS))
+    futures = {job: pool.apply_async(_oracle_job, (job,)) for job in JOBS}
+    yield futures
+    pool.terminate()
+    pool.join()
+
+
 @pytest.fixture(scope="module")
 def graph():
     if not torch.cuda.is_available():
@@ -30,7 +63,7 @@ def graph():
 
 
 @pytest.fixture(scope="module")
-def gpu(graph):
+def gpu(graph, oracle_results):
     import paper_2306_08623_gb300.nucleus as nc
     off, adj = graph
     d_off = torch.from_numpy(off).cuda()
@@ -40,16 +73,22 @@ def gpu(graph):
     return nc, o, ris
 
 
-def run_pair(gpu, r, s, deltas=()):
+def run_pair(gpu, r, s, method, deltas=()):
     nc, o, ris = gpu
     ri = ris[r]
     cnt, n_s = nc.count_s_cliques(o, ri, s)
-    pk = nc.peel_and_link(o, ri, s, cnt, stats=True)
-    parent, label, nn = nc.construct_tree(pk["core"], pk["uf"], pk["L"])
+    if method == "el":
+        pk = nc.peel_and_link(o, ri, s, cnt, stats=True)
+        parent, label, nn = nc.construct_tree(pk["core"], pk["uf"], pk["L"])
+    else:
+        pk = nc.peel_cores(o, ri, s, cnt, stats=True)
+        parent, label, nn = nc.hierarchy_two_phase(o, ri, s, pk["core"])
     out = {"n_r": ri.n_r, "n_s": n_s, "cnt": u32(cnt), "core": u32(pk["core"]), "round": u32(pk["round"]),
            "parent": parent.cpu().numpy(), "label": u32(label), "n_nodes": nn, "stats": pk["stats"]}
     for d in deltas:
-        out["approx_%g" % d] = u32(nc.approx_nucleus(o, ri, s, d, cnt)["approx"])
+        a = nc.approx_nucleus(o, ri, s, d, cnt, stats=True)
+        out["approx_%g" % d] = u32(a["approx"])
+        out["approx_rounds_%g" % d] = a["stats"]["rounds"]
     return out
 
 
@@ -71,45 +110,60 @@ def global_properties(g, r, s):
 
 
 @pytest.mark.parametrize("r,s", [(1, 2), (2, 3)])
-def test_full_parity(graph, gpu, r, s):
+def test_full_parity(graph, gpu, oracle_results, r, s):
     off, adj = graph
-    g = run_pair(gpu, r, s)
-    ref = oracle.nucleus(off, adj, r, s, hier="def")
-    assert g["n_r"] == ref["n_r"] and g["n_s"] == ref["n_s"]
-    assert np.array_equal(g["cnt"], ref["cnt"])
-    assert np.array_equal(g["core"], ref["core"])
-    compare_hierarchy(g["parent"], g["label"], g["n_nodes"], ref["leaf_node"], ref["node_parent"],
-                      ref["node_label"])
-    global_properties(g, r, s)
+    ref = oracle_results[("exact", r, s, None)].get(timeout=1800)
+    for method in ("te", "el"):
+        g = run_pair(gpu, r, s, method)
+        assert g["n_r"] == ref["n_r"] and g["n_s"] == ref["n_s"]
+        assert np.array_equal(g["cnt"], ref["cnt"])
+        assert np.array_equal(g["core"], ref["core"])
+        compare_hierarchy(g["parent"], g["label"], g["n_nodes"], ref["leaf_node"], ref["node_parent"],
+                          ref["node_label"])
+        global_properties(g, r, s)
 
 
-@pytest.mark.parametrize("r,s", [(2, 4), (3, 4)])
-def test_sampled_certificate(graph, gpu, r, s):
+def test_approx_23_bit_exact_full_size(gpu, oracle_results):
+    """Alg. 2 on the benchmark graph's (2,3): values and round counts equal the oracle's."""
+    g = run_pair(gpu, 2, 3, "te", deltas=(0.1, 0.5))
+    for d in (0.1, 0.5):
+        ra = oracle_results[("approx", 2, 3, d)].get(timeout=1800)
+        assert np.array_equal(g["approx_%g" % d], ra["approx"]), d
+        assert g["approx_rounds_%g" % d] == ra["approx_rounds"]
+
+
+def _tuples_match(nc, ris, r, off, adj):
+    """the lexicographic r-clique order the certificate assumes is the GPU's"""
+    got = nc.rindex_tuples(ris[r]).cpu().numpy().reshape(-1, r)
+    if r == 2:
+        assert np.array_equal(got, gg.edge_list(off, adj).astype(np.int32))
+    else:
+        assert (np.diff(got, axis=1) > 0).all()
+        key = (got[:, 0].astype(np.int64) << 36) | (got[:, 1].astype(np.int64) << 18) | got[:, 2]
+        assert (np.diff(key) > 0).all()
+
+
+@pytest.mark.parametrize("r,s,method", [(2, 4, "te"), (3, 4, "el"), (3, 4, "te")])
+def test_certified_on_every_r_clique(graph, gpu, r, s, method):
+    """Every r-clique and every s-clique of the full-size (2,4) / (3,4) decomposition satisfies
+    the local certificate: the core numbers are exact and the hierarchy is the definitional one."""
     off, adj = graph
     nc, o, ris = gpu
-    g = run_pair(gpu, r, s)
+    g = run_pair(gpu, r, s, method)
     global_properties(g, r, s)
-    tuples = nc.rindex_tuples(ris[r]).cpu().numpy().reshape(-1, r)
-    rng = np.random.default_rng(2024 + r)
-    n_r = g["n_r"]
-    top = np.argsort(g["core"])[-300:]                        # the densest part, where ties are
-    sample = np.unique(np.concatenate([rng.choice(n_r, size=1500, replace=False), top]))
-    # the checker's lookups need the lexicographic r-clique table: the oracle builds its own
-    rtab = oracle.list_cliques(off, adj, r) if r < 3 else tuples_from_oracle(off, adj)
-    assert np.array_equal(rtab, tuples)
-    bad = oracle.check_sample(off, adj, r, s, rtab, sample, cnt=g["cnt"], core=g["core"], rnd=g["round"],
-                              parent=g["parent"], label=g["label"])
-    assert bad.tolist() == [0, 0, 0, 0], bad
+    _tuples_match(nc, ris, r, off, adj)
+    cert = oracle.certify(off, adj, r, s, g["n_r"], cnt=g["cnt"], core=g["core"], rnd=g["round"],
+                          parent=g["parent"][: g["n_r"] + g["n_nodes"]], label=g["label"][: g["n_nodes"]],
+                          n_nodes=g["n_nodes"], threads=min(16, os.cpu_count() or 1))
+    assert cert["hierarchy_checked"]
+    assert cert["n_s"] == g["n_s"]
+    bad = {k: cert[k] for k in ("count", "validity", "peel_order", "under_merge", "over_merge")}
+    assert all(v == 0 for v in bad.values()), bad
 
 
-def tuples_from_oracle(off, adj):
-    return oracle.list_cliques(off, adj, 3)
-
-
-@pytest.mark.parametrize("r,s", [(2, 3), (3, 4)])
-def test_approx_bound_full_size(graph, gpu, r, s):
-    g = run_pair(gpu, r, s, deltas=(0.1, 0.5))
-    C = comb(s, r)
+def test_approx_bound_full_size_34(gpu):
+    g = run_pair(gpu, 3, 4, "te", deltas=(0.1, 0.5))
+    C = comb(4, 3)
     core = g["core"].astype(np.float64)
     nz = core > 0
     for d in (0.1, 0.5):
@@ -118,21 +172,3 @@ def test_approx_bound_full_size(graph, gpu, r, s):
         assert (ap[nz] >= core[nz]).all()
         assert (ap[nz] <= (C + d) * (1 + d) * core[nz] + 1e-9).all()
         assert (ap <= g["cnt"]).all()
-
-
-@pytest.mark.parametrize("r,s", [(1, 2), (2, 3), (2, 4)])
-def test_two_phase_full_size(graph, gpu, r, s):
-    """The bench builds these pairs with the two-phase hierarchy (cores-only peel, then §7.4):
-    at full size its core numbers and round stamps equal the linking peel's, and its hierarchy
-    equals the linking peel's tree, which the tests above tie to the oracle."""
-    nc, o, ris = gpu
-    ri = ris[r]
-    cnt, _ = nc.count_s_cliques(o, ri, s)
-    el = nc.peel_and_link(o, ri, s, cnt)
-    p_el, l_el, nn_el = nc.construct_tree(el["core"], el["uf"], el["L"])
-    te = nc.peel_cores(o, ri, s, cnt)
-    assert torch.equal(te["core"], el["core"]) and torch.equal(te["round"], el["round"])
-    p_te, l_te, nn_te = nc.hierarchy_two_phase(o, ri, s, te["core"])
-    n_r = ri.n_r
-    p_el = p_el.cpu().numpy()
-    compare_hierarchy(p_te.cpu().numpy(), u32(l_te), nn_te, p_el[:n_r], p_el[n_r:n_r + nn_el], u32(l_el))
