@@ -31,12 +31,13 @@ extern "C" {
 int nh_debug_inject(int what, int64_t value);
 
 /* Round trace of the persistent peel kernels (nh_peel_and_link, nh_approx_nucleus): when set, the
- * next peels write, for every round t = 1, 2, ... (while t <= cap), four words at log[4 (t-1)]:
+ * next peels write, for every round t = 1, 2, ... (while t <= cap), eight words at log[8 (t-1)]:
  * (frontier size << 32 | levels opened so far), the device global timer (ns) at the end of the
- * round, the out-list entries the (2,4) triangle-list re-listing expanded in the round, and
- * (its sub-tasks << 32 | of which block sub-tasks).  log: device uint64[4 cap], owned by the
- * caller and kept alive while set; NULL or cap 0 turns the trace off.  Returns NH_OK or
- * NH_ERR_INVALID (cap < 0). */
+ * round, the out-list entries the (2,4) triangle-list re-listing expanded in the round,
+ * (its sub-tasks << 32 | of which block sub-tasks), then block 0's timer when that re-listing
+ * starts, after it split the round into sub-tasks, after its warp phase and at its end (0 for
+ * the other re-listings).  log: device uint64[8 cap], owned by the caller and kept alive while
+ * set; NULL or cap 0 turns the trace off.  Returns NH_OK or NH_ERR_INVALID (cap < 0). */
 int nh_debug_round_log(uint64_t* log, int64_t cap);
 
 #ifdef __cplusplus

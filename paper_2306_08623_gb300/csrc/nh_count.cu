@@ -16,10 +16,12 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
   return v;
 }
 
-// cnt[x] += inc with a check that the uint32 count does not wrap (status NH_ERR_COUNT_OVERFLOW)
+// cnt[x] += inc (a reduction: the old value is not needed).  A count that passes 2^32 - 1 wraps
+// and loses exactly 2^32, which the check after the count (k_count_check) sees in the sum of all
+// counts; status is unused here.
 __device__ __forceinline__ void cnt_add(uint32_t* cnt, int64_t x, uint32_t inc, int* status) {
-  const uint32_t old = atomicAdd(&cnt[x], inc);
-  if (old > 0xffffffffu - inc) atomicCAS(status, 0, NH_ERR_COUNT_OVERFLOW);
+  (void)status;
+  atomicAdd(&cnt[x], inc);
 }
 
 __device__ __forceinline__ void tri_add(const GView& g, unsigned long long key, uint32_t inc, uint32_t* cnt,
@@ -217,6 +219,23 @@ int grid_for(const void* fn, int threads, size_t smem) {
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 
+// Overflow check after counting: every s-clique adds 1 to each of its C r-subsets, so the counts
+// sum to base * n_r + C * n_s (base: their initial value).  A count that wrapped lost a multiple
+// of 2^32, which the 64-bit sum of the stored counts shows.  sums[0] accumulates the sum.
+__global__ void k_count_sum(int64_t n, const uint32_t* __restrict__ cnt, unsigned long long* __restrict__ sums) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += cnt[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(NH_FULL, s, d);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(sums, s);
+}
+
+__global__ void k_count_check(const unsigned long long* __restrict__ sums, const unsigned long long* __restrict__ n_s,
+                              int64_t n_r, unsigned long long C, unsigned long long base, int* __restrict__ status) {
+  if (sums[0] != base * (unsigned long long)n_r + C * n_s[0]) atomicCAS(status, 0, NH_ERR_COUNT_OVERFLOW);
+}
+
 __global__ void k_fill_u32(int64_t n, uint32_t* __restrict__ a, uint32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
 }
@@ -274,6 +293,17 @@ int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t*
     else if (r == 2) k_count_s4<2><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
     else k_count_s4<3><<<grid, kThreads, dyn, st>>>(g, cnt, dcount, scratch, cap, use_smem, status, order, next, measure);
     nh_note_launch();
+  }
+  if (!rc && ri->n_r > 0) {
+    unsigned long long* sums = nullptr;
+    if (!(rc = nh_alloc(&sums, 1, st))) {
+      cudaMemsetAsync(sums, 0, sizeof(unsigned long long), st);
+      k_count_sum<<<nh_blocks_for(ri->n_r, 256, 152 * 8), 256, 0, st>>>(ri->n_r, cnt, sums);
+      k_count_check<<<1, 1, 0, st>>>(sums, dcount, ri->n_r, (unsigned long long)nh_binom(s, r),
+                                     (unsigned long long)g_nh_inject_count_base, status);
+      nh_note_launch(2);
+      nh_free(sums, st);
+    }
   }
   if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
   nh_free(scratch, st); nh_free(order, st); nh_free(next, st);

@@ -44,7 +44,9 @@ struct PeelCtl {
   unsigned long long task_next;     // next re-listing task of the round (work-proportional mode)
   unsigned long long c24_next;      // (2,4) triangle-list re-listing: next list item for warps,
   unsigned long long c24_hn;        // entries pushed to the block queue,
-  unsigned long long c24_hk;        // entries taken from it
+  unsigned long long c24_hk;        // tickets taken for it
+  unsigned int c24_done;            // blocks whose warps finished pushing to it this round
+  unsigned int c24_pad;
   unsigned long long c24_tasks;     // sub-tasks of the round (round trace)
   unsigned long long dbg_work;      // list entries expanded in the round (round trace)
   // statistics
@@ -161,6 +163,39 @@ __device__ __forceinline__ bool grid_sync(PeelCtl* ctl, unsigned long long timeo
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The control words a round needs, copied to shared memory by one thread after each grid barrier:
+// independent loads from L2 instead of one dependent volatile read per field and thread.
+struct RoundView {
+  unsigned int done, err, need_scan, t, thr, cur, alive_cur, draining, drain_buf;
+  unsigned long long fsize, alive_n, drain_n;
+};
+
+__device__ __forceinline__ void round_view_load(PeelCtl* c, RoundView* v) {
+  RoundView x;
+  x.done = __ldcg(reinterpret_cast<const unsigned int*>(&c->done));
+  x.err = __ldcg(reinterpret_cast<const unsigned int*>(&c->err));
+  x.need_scan = __ldcg(&c->need_scan);
+  x.t = __ldcg(&c->t);
+  x.thr = __ldcg(&c->thr);
+  x.cur = __ldcg(&c->cur);
+  x.alive_cur = __ldcg(&c->alive_cur);
+  x.draining = __ldcg(&c->draining);
+  x.drain_buf = __ldcg(&c->drain_buf);
+  x.fsize = __ldcg(&c->fsize);
+  x.alive_n = __ldcg(&c->alive_n);
+  x.drain_n = __ldcg(&c->drain_n);
+  *v = x;
+}
+
+// grid_sync, then the round view refreshed in shared memory (block-collective)
+template <class F>
+__device__ __forceinline__ bool grid_sync_view(PeelCtl* ctl, unsigned long long timeout_ns, RoundView* v, F leader) {
+  const bool ok = grid_sync(ctl, timeout_ns, leader);
+  if (threadIdx.x == 0) round_view_load(ctl, v);
+  __syncthreads();
+  return ok;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -879,9 +914,11 @@ __device__ __forceinline__ void relist_list(const PeelArgs& A, const int32_t* it
   unsigned long long it = (unsigned long long)grp;
   // one warp per r-clique: r-cliques in batches from the shared counter (per-r-clique work is
   // heavy-tailed, so a fixed stride would leave the round to its unluckiest warp)
-  const unsigned long long dper = n / ((unsigned long long)nwarps * 16ull);
+  const unsigned long long dNW = (unsigned long long)nwarps;
+  const unsigned long long drest = n > dNW ? n - dNW : 0ull;
+  const unsigned long long dper = drest / (dNW * 16ull);
   const unsigned long long dbt = dper > 0 ? dper : 1ull;
-  unsigned long long dk = 0, dk1 = 0;
+  unsigned long long dk = (unsigned long long)gwarp, dk1 = dk + 1;  // r-clique gwarp first
   int32_t curR = -1;
   for (;;) {
     int32_t Rid;
@@ -915,13 +952,14 @@ __device__ __forceinline__ void relist_list(const PeelArgs& A, const int32_t* it
       k += run;
     } else if (G == 1) {
       if (dk >= dk1) {
+        if (drest == 0) break;
         unsigned long long k0 = 0;
         if (lane == 0) k0 = atomicAdd(task_next, dbt);
-        k0 = __shfl_sync(NH_FULL, k0, 0);
-        if (k0 >= n) break;
+        k0 = dNW + __shfl_sync(NH_FULL, k0, 0);
         dk = k0;
         dk1 = k0 + dbt < n ? k0 + dbt : n;
       }
+      if (dk >= n) break;
       Rid = __ldcg(items + dk);
       ++dk;
       c0 = 0;
@@ -963,74 +1001,91 @@ namespace nhp {
 // the persistent kernel
 // ---------------------------------------------------------------------------------------------
 
+// The leaders run in the last block to reach a grid barrier, while every other block waits: they
+// read every control word they need at once (independent loads from L2), then write the next
+// round's words.
 template <bool EXACT>
 __device__ void leader_after_scan(const PeelArgs& A) {
   PeelCtl* c = A.lk.ctl;
-  const unsigned int gm = c->gmin;
+  const unsigned int gm = __ldcg(&c->gmin), ac = __ldcg(&c->alive_cur), thr0 = __ldcg(&c->thr);
+  const unsigned int bucket0 = __ldcg(&c->bucket);
+  const unsigned long long a2 = __ldcg(&c->alive2_count), lv = __ldcg(&c->st_levels);
   c->gmin = kNone;
-  c->alive_cur ^= 1u;
-  c->alive_n = c->alive2_count;
+  c->alive_cur = ac ^ 1u;
+  c->alive_n = a2;
   c->alive2_count = 0;
   c->f_count = 0;
   if (EXACT) {
-    if (gm != kNone && gm > c->thr) c->thr = gm;
+    if (gm != kNone && gm > thr0) c->thr = gm;
   } else {
-    while ((int)c->bucket + 1 < A.n_thr && A.thresholds[c->bucket] < gm) {
-      c->bucket++;
+    unsigned int b = bucket0;
+    while ((int)b + 1 < A.n_thr && A.thresholds[b] < gm) b++;
+    if (b != bucket0) {
+      c->bucket = b;
       c->rounds_in_bucket = 0;
     }
-    c->thr = A.thresholds[c->bucket];
+    c->thr = A.thresholds[b];
   }
-  c->st_levels++;
+  c->st_levels = lv + 1;
 }
 
 template <bool EXACT>
 __device__ void leader_end_of_round(const PeelArgs& A) {
   PeelCtl* c = A.lk.ctl;
+  const unsigned int oc = __ldcg(&c->ovf_cur), thr = __ldcg(&c->thr), kmax = __ldcg(&c->kmax);
+  const unsigned int t = __ldcg(&c->t), cur = __ldcg(&c->cur), rib = __ldcg(&c->rounds_in_bucket);
+  const unsigned int bucket = __ldcg(&c->bucket);
+  const unsigned long long ov0 = __ldcg(&c->ovf_count[0]), ov1 = __ldcg(&c->ovf_count[1]);
+  const unsigned long long finished = __ldcg(&c->finished), fsize = __ldcg(&c->fsize);
+  const unsigned long long rounds = __ldcg(&c->st_rounds), front = __ldcg(&c->st_front);
+  const unsigned long long nfc = __ldcg(&c->nf_count), hn = __ldcg(&c->c24_hn);
   c->task_next = 0;
   c->c24_next = 0;
   c->c24_hn = 0;
   c->c24_hk = 0;
-  const unsigned int oc = c->ovf_cur;
-  if (c->ovf_count[oc] > 0) {
+  c->c24_done = 0;
+  const unsigned long long ovc = oc ? ov1 : ov0;
+  if (ovc > 0) {
     c->draining = 1;
     c->drain_buf = oc;
-    c->drain_n = c->ovf_count[oc] < A.lk.ovf_cap ? c->ovf_count[oc] : A.lk.ovf_cap;
+    c->drain_n = ovc < A.lk.ovf_cap ? ovc : A.lk.ovf_cap;
     c->ovf_count[oc] = 0;
     c->ovf_cur = oc ^ 1u;
     return;
   }
   c->draining = 0;
-  c->finished += c->fsize;
-  if (A.round_log && c->st_rounds < A.round_log_cap) {
-    unsigned long long* L = A.round_log + 4 * c->st_rounds;
-    L[0] = (c->fsize << 32) | (c->st_levels & 0xffffffffull);
+  c->finished = finished + fsize;
+  if (A.round_log && rounds < A.round_log_cap) {
+    unsigned long long* L = A.round_log + 8 * rounds;
+    L[0] = (fsize << 32) | (__ldcg(&c->st_levels) & 0xffffffffull);
     L[1] = nh_globaltimer();
-    L[2] = c->dbg_work;
-    L[3] = (c->c24_tasks << 32) | (c->c24_hn & 0xffffffffull);
+    L[2] = __ldcg(&c->dbg_work);
+    L[3] = (__ldcg(&c->c24_tasks) << 32) | (hn & 0xffffffffull);
     c->dbg_work = 0;
   }
-  c->st_rounds++;
-  c->st_front += c->fsize;
-  if (c->thr > c->kmax && c->fsize > 0) c->kmax = c->thr;
-  c->t++;
-  if (c->finished >= (unsigned long long)A.n_r) {
+  c->st_rounds = rounds + 1;
+  c->st_front = front + fsize;
+  if (thr > kmax && fsize > 0) c->kmax = thr;
+  c->t = t + 1;
+  if (finished + fsize >= (unsigned long long)A.n_r) {
     c->done = 1;
     return;
   }
   if (!EXACT) {
-    if (++c->rounds_in_bucket >= A.T) {
-      if ((int)c->bucket + 1 < A.n_thr) c->bucket++;
+    if (rib + 1 >= A.T) {
+      const unsigned int b = ((int)bucket + 1 < A.n_thr) ? bucket + 1 : bucket;
+      c->bucket = b;
       c->rounds_in_bucket = 0;
-      c->thr = A.thresholds[c->bucket];
+      c->thr = A.thresholds[b];
       c->need_scan = 1;
       c->nf_count = 0;
       return;
     }
+    c->rounds_in_bucket = rib + 1;
   }
-  if (c->nf_count > 0) {
-    c->cur ^= 1u;
-    c->fsize = c->nf_count;
+  if (nfc > 0) {
+    c->cur = cur ^ 1u;
+    c->fsize = nfc;
     c->nf_count = 0;
     c->need_scan = 0;
   } else {
@@ -1043,10 +1098,11 @@ __device__ void leader_end_of_round(const PeelArgs& A) {
 template <int R, int S>
 constexpr int min_blocks() { return (R == 2 && S == 4) ? 3 : kMinBlocks; }
 
-template <int R, int S, bool EXACT>
+// C24: the (2,4) triangle-list re-listing (nh_relist24.cuh) in place of the adjacency / chunk-task
+// path, as its own instantiation so that neither carries the other's registers
+template <int R, int S, bool EXACT, bool C24>
 __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs A) {
   PeelCtl* ctl = A.lk.ctl;
-  volatile PeelCtl* vc = ctl;
   const int lane = threadIdx.x & 31;
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1057,20 +1113,24 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
   int32_t* s_seen = reinterpret_cast<int32_t*>(s_dyn + kSmSeen);
   unsigned long long* s_wsum = reinterpret_cast<unsigned long long*>(s_dyn + kSmWsum);
   int* s_lcnt = reinterpret_cast<int*>(s_dyn + kSmLcnt);
-  const bool use24 = (R == 2 && S == 4) && A.use24;
+  constexpr bool use24 = C24;
   if (!use24 && lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
   const WarpLinks W{s_links + (threadIdx.x >> 5) * kLinkBuf, &s_lcnt[threadIdx.x >> 5], s_seen + (threadIdx.x >> 5) * kSeen};
+  __shared__ RoundView s_rv;
+  if (threadIdx.x == 0) round_view_load(ctl, &s_rv);
+  __syncthreads();
+  const RoundView& rv = s_rv;
   for (;;) {
-    if (vc->done || vc->err) break;
-    if (vc->need_scan) {
+    if (rv.done || rv.err) break;
+    if (rv.need_scan) {
       // compact the live list and take the minimum count over it
       {
-        const unsigned int ac = vc->alive_cur;
+        const unsigned int ac = rv.alive_cur;
         const int32_t* ain = A.alive[ac];
         int32_t* aout = A.alive[ac ^ 1u];
-        const unsigned long long na = vc->alive_n;
-        const unsigned int t = vc->t;
+        const unsigned long long na = rv.alive_n;
+        const unsigned int t = rv.t;
         uint32_t lmin = kNone;
         for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
              base += (unsigned long long)nwarps * 32) {
@@ -1089,13 +1149,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
         lmin = warp_min_u32(lmin);
         if (lane == 0 && lmin != kNone) atomicMin(&ctl->gmin, lmin);
       }
-      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_after_scan<EXACT>(A); })) break;
+      if (!grid_sync_view(ctl, A.timeout_ns, &s_rv, [&] { leader_after_scan<EXACT>(A); })) break;
       // frontier = live with count <= threshold
       {
-        const int32_t* al = A.alive[vc->alive_cur];
-        const unsigned long long na = vc->alive_n;
-        const unsigned int thr = vc->thr, t = vc->t;
-        int32_t* fr = A.front[vc->cur];
+        const int32_t* al = A.alive[rv.alive_cur];
+        const unsigned long long na = rv.alive_n;
+        const unsigned int thr = rv.thr, t = rv.t;
+        int32_t* fr = A.front[rv.cur];
         for (unsigned long long base = (unsigned long long)gwarp * 32; base < na;
              base += (unsigned long long)nwarps * 32) {
           const unsigned long long i = base + lane;
@@ -1113,20 +1173,22 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
           }
         }
       }
-      if (!grid_sync(ctl, A.timeout_ns, [&] {
-            ctl->fsize = ctl->f_count;
+      if (!grid_sync_view(ctl, A.timeout_ns, &s_rv, [&] {
+            ctl->fsize = __ldcg(&ctl->f_count);
             ctl->f_count = 0;
           }))
         break;
     }
     // re-list the frontier
     {
-      const unsigned int t = vc->t, thr = vc->thr, cur = vc->cur;
-      const unsigned long long fs = vc->fsize;
+      const unsigned int t = rv.t, thr = rv.thr, cur = rv.cur;
+      const unsigned long long fs = rv.fsize;
       const int32_t* fr = A.front[cur];
       int32_t* nf = A.front[cur ^ 1u];
-      if (use24) {
-        c24_list<EXACT>(A, fr, fs, t, thr, nf, nwarps, s_dyn, ls);
+      if constexpr (use24) {
+        if (A.round_log && blockIdx.x == 0 && threadIdx.x == 0 && t >= 1 && t <= A.round_log_cap)
+          A.round_log[8 * (t - 1) + 4] = nh_globaltimer();
+        c24_list<EXACT>(A, fr, fs, t, thr, nf, gwarp, nwarps, s_dyn, ls);
       } else {
         unsigned long long total = 0;
         const bool tasks = fs <= (unsigned long long)A.task_items &&
@@ -1138,14 +1200,16 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
     // end of round: drain deferred link calls, then advance
     bool ok = true;
     for (;;) {
-      if (!grid_sync(ctl, A.timeout_ns, [&] { leader_end_of_round<EXACT>(A); })) { ok = false; break; }
-      if (!vc->draining) break;
-      const int2* q = A.lk.ovf[vc->drain_buf];
-      const unsigned long long nq = vc->drain_n;
-      for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-           i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int2 p = __ldcg(q + i);
-        add_delta(ls, link_run_call(A.lk, p.x, p.y));
+      if (!grid_sync_view(ctl, A.timeout_ns, &s_rv, [&] { leader_end_of_round<EXACT>(A); })) { ok = false; break; }
+      if (!rv.draining) break;
+      if constexpr (!C24) {  // the triangle-list re-listing never links, so never defers a call
+        const int2* q = A.lk.ovf[rv.drain_buf];
+        const unsigned long long nq = rv.drain_n;
+        for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+             i += (unsigned long long)gridDim.x * blockDim.x) {
+          const int2 p = __ldcg(q + i);
+          add_delta(ls, link_run_call(A.lk, p.x, p.y));
+        }
       }
     }
     if (!ok) break;
@@ -1169,7 +1233,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
 
 template <int R, int S, bool EXACT>
 int launch_peel(PeelArgs& A, cudaStream_t st) {
-  const void* fn = (const void*)k_peel<R, S, EXACT>;
+  const void* fn = (const void*)k_peel<R, S, EXACT, false>;
+  if constexpr (R == 2 && S == 4) {
+    if (A.use24) fn = (const void*)k_peel<R, S, EXACT, true>;
+  }
   int dev = 0, sms = 0, per = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1208,7 +1275,7 @@ struct TreeOut {
   unsigned long long* node_count;
 };
 
-template <int R, int S>
+template <int R, int S, bool C24>
 __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(PeelArgs A, TreeOut T) {
   PeelCtl* ctl = A.lk.ctl;
   volatile PeelCtl* vc = ctl;
@@ -1224,7 +1291,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(Peel
   int32_t* s_seen = reinterpret_cast<int32_t*>(s_dyn + kSmSeen);
   unsigned long long* s_wsum = reinterpret_cast<unsigned long long*>(s_dyn + kSmWsum);
   int* s_lcnt = reinterpret_cast<int*>(s_dyn + kSmLcnt);
-  const bool use24 = (R == 2 && S == 4) && A.use24;
+  constexpr bool use24 = C24;
   if (!use24 && lane == 0) s_lcnt[threadIdx.x >> 5] = 0;
   __syncwarp();
   const WarpLinks W{s_links + (threadIdx.x >> 5) * kLinkBuf, &s_lcnt[threadIdx.x >> 5], s_seen + (threadIdx.x >> 5) * kSeen};
@@ -1234,8 +1301,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(Peel
     const unsigned long long cnt = (unsigned long long)(hi - lo);
     if (cnt == 0) continue;
     // unions at this level
-    if (use24) {
-      c24_list<true>(A, T.order + lo, cnt, 0u, level, nullptr, nwarps, s_dyn, ls);
+    if constexpr (use24) {
+      c24_list<true>(A, T.order + lo, cnt, 0u, level, nullptr, gwarp, nwarps, s_dyn, ls);
     } else {
       unsigned long long total = 0;
       const bool tasks = cnt <= (unsigned long long)A.task_items &&
@@ -1248,6 +1315,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(Peel
           ctl->c24_next = 0;
           ctl->c24_hn = 0;
           ctl->c24_hk = 0;
+          ctl->c24_done = 0;
         }))
       break;
     // a node for every component holding an r-clique of this level (with labels that are not
@@ -1307,7 +1375,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_two_phase(Peel
 
 template <int R, int S>
 int launch_two_phase(PeelArgs& A, TreeOut& T, cudaStream_t st) {
-  const void* fn = (const void*)k_two_phase<R, S>;
+  const void* fn = (const void*)k_two_phase<R, S, false>;
+  if constexpr (R == 2 && S == 4) {
+    if (A.use24) fn = (const void*)k_two_phase<R, S, true>;
+  }
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -297,11 +297,46 @@ __device__ __forceinline__ void c24_stage(const PeelArgs& A, int32_t Rid, uint32
   }
 }
 
-// One scan entry q of the out-list of a w (flags wfl): if its x is staged, {a, b, w, x} is an
-// s-clique.  Peel: a live s-clique of R's is counted on x's staged position and on *wslot (w's
-// position, or a w-side accumulator), and {w,x} is decremented at once (cross / e: a crossing to
-// append); with xdirect the x side is decremented at once as well (cxa / xa, cxb / xb).
-// Hierarchy: unions with {w,x} and marks on the positions.
+// The s-clique {a, b, w, x} of a scan entry whose x is staged at position px, given its edge e =
+// {w, x} and e's round stamp (peel) or core number (hierarchy) v.  Peel: if it is live and R's, it
+// is counted on x's staged position and on *wslot (w's position, or a w-side accumulator), and e
+// is decremented at once (cross: a crossing to append); with xdirect the x side is decremented at
+// once as well (cxa / xa, cxb / xb).  Hierarchy: unions with e and marks on the positions.
+template <bool EXACT>
+__device__ __forceinline__ void c24_pair_apply(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr,
+                                               const C24Area& G, int px, int32_t e, uint32_t v, uint32_t wfl,
+                                               uint32_t* wslot, bool xdirect, int64_t xrel_base, bool& in_level,
+                                               bool& cross, bool& cxa, int32_t& xa, bool& cxb, int32_t& xb,
+                                               LocalStats& ls) {
+  if (A.union_mode) {
+    if (v >= thr) {
+      in_level = true;
+      if (!(wfl & kSpoil) && !(G.meta[px] & kSpoil) && !(v == thr && e < Rid)) {
+        ls.listed++;
+        atomicOr(wslot, 1u);
+        atomicOr(&G.meta[px], 1u);
+        c24_unite(A, Rid, e, ls);
+      }
+    }
+    return;
+  }
+  if ((v != 0u && v < t) || (v == t && e < Rid)) return;
+  ls.listed++;
+  atomicAdd(wslot, 1u);
+  if (!xdirect) {
+    atomicAdd(&G.meta[px], 1u);
+  } else {  // the x side per s-clique (its sums could exceed the meta field)
+    const uint32_t mx = G.meta[px];
+    const int64_t jx = xrel_base + (mx >> 16);
+    xa = __ldg(A.g.t2ea + jx);
+    xb = __ldg(A.g.t2eb + jx);
+    if (mx & kDecA) cxa = c24_dec<EXACT>(A, xa, 1u, t, thr, ls);
+    if (mx & kDecB) cxb = c24_dec<EXACT>(A, xb, 1u, t, thr, ls);
+  }
+  if (v == 0u || v > t) cross = c24_dec<EXACT>(A, e, 1u, t, thr, ls);
+}
+
+// One scan entry q of the out-list of a w (flags wfl), see c24_pair_apply.
 template <bool EXACT>
 __device__ __forceinline__ void c24_pair(const PeelArgs& A, int32_t Rid, uint32_t t, uint32_t thr, const C24Area& G,
                                          int64_t q, uint32_t wfl, uint32_t* wslot, bool xdirect, int64_t xrel_base,
@@ -315,34 +350,9 @@ __device__ __forceinline__ void c24_pair(const PeelArgs& A, int32_t Rid, uint32_
   if (px < 0) return;
   e = eq;
   ls.stamp++;
-  if (A.union_mode) {
-    const uint32_t ce = __ldcg(A.val + e);
-    if (ce >= thr) {
-      in_level = true;
-      if (!(wfl & kSpoil) && !(G.meta[px] & kSpoil) && !(ce == thr && e < Rid)) {
-        ls.listed++;
-        atomicOr(wslot, 1u);
-        atomicOr(&G.meta[px], 1u);
-        c24_unite(A, Rid, e, ls);
-      }
-    }
-    return;
-  }
-  const uint32_t re = __ldcg(A.round + e);
-  if ((re != 0u && re < t) || (re == t && e < Rid)) return;
-  ls.listed++;
-  atomicAdd(wslot, 1u);
-  if (!xdirect) {
-    atomicAdd(&G.meta[px], 1u);
-  } else {  // the x side per s-clique (its sums could exceed the meta field)
-    const uint32_t mx = G.meta[px];
-    const int64_t jx = xrel_base + (mx >> 16);
-    xa = __ldg(A.g.t2ea + jx);
-    xb = __ldg(A.g.t2eb + jx);
-    if (mx & kDecA) cxa = c24_dec<EXACT>(A, xa, 1u, t, thr, ls);
-    if (mx & kDecB) cxb = c24_dec<EXACT>(A, xb, 1u, t, thr, ls);
-  }
-  if (re == 0u || re > t) cross = c24_dec<EXACT>(A, e, 1u, t, thr, ls);
+  const uint32_t v = __ldcg(c24_vals(A) + e);
+  c24_pair_apply<EXACT>(A, Rid, t, thr, G, px, e, v, wfl, wslot, xdirect, xrel_base, in_level, cross, cxa, xa, cxb,
+                        xb, ls);
 }
 
 // appends this step's crossings to the next frontier (warp-collective)
@@ -484,21 +494,60 @@ __device__ void c24_item(const PeelArgs& A, int32_t Rid, int sub, int nsub, uint
     const unsigned long long xa0 = (unsigned long long)sub * xstep;
     const uint32_t x0 = xa0 < E ? (uint32_t)xa0 : E;
     const uint32_t x1 = x0 + xstep < E ? x0 + xstep : E;
-    for (uint32_t cb = x0 + (uint32_t)wit * 32; cb < x1; cb += TEAM) {
-      const uint32_t idx = cb + lane;
-      bool cross = false, cxa = false, cxb = false;
-      int32_t e = 0, xa = 0, xb = 0;
-      if (idx < x1) {
-        int plo = 0, phi = nc;  // first position whose inclusive prefix exceeds idx
-        while (plo < phi) {
-          const int mid = (plo + phi) >> 1;
-          if (G.epre[mid] <= idx) plo = mid + 1; else phi = mid;
+    // two scan entries per lane and step, their loads issued together
+    const uint32_t* vals = c24_vals(A);
+    for (uint32_t cb = x0 + (uint32_t)wit * 64; cb < x1; cb += 2 * TEAM) {
+      int pw[2], px[2];
+      int32_t e[2];
+      uint32_t v[2];
+      int64_t q[2];
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const uint32_t idx = cb + 32 * k + lane;
+        pw[k] = -1;
+        q[k] = 0;
+        if (idx < x1) {
+          int plo = 0, phi = nc;  // first position whose inclusive prefix exceeds idx
+          while (plo < phi) {
+            const int mid = (plo + phi) >> 1;
+            if (G.epre[mid] <= idx) plo = mid + 1; else phi = mid;
+          }
+          pw[k] = plo;
+          q[k] = (int64_t)G.ob[plo] + (idx - (plo ? G.epre[plo - 1] : 0u));
         }
-        const uint32_t start = plo ? G.epre[plo - 1] : 0u;
-        c24_pair<EXACT>(A, Rid, t, thr, G, (int64_t)G.ob[plo] + (idx - start), G.meta[plo], &G.meta[plo], false, 0,
-                        in_level, cross, e, cxa, xa, cxb, xb, ls);
       }
-      c24_append(A, nf, false, cross, e, cxa, xa, cxb, xb);
+      int32_t xv[2];
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        xv[k] = 0;
+        e[k] = 0;
+        if (pw[k] >= 0) {
+          xv[k] = __ldg(A.g.oadj + q[k]);
+          e[k] = __ldg(A.g.oeid + q[k]);
+          ls.scan += 2;
+          ls.expand++;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        px[k] = pw[k] >= 0 ? c24_find(G, xv[k]) : -1;
+        v[k] = 0;
+        if (px[k] >= 0) {
+          v[k] = __ldcg(vals + e[k]);
+          ls.stamp++;
+        }
+      }
+      bool cross[2] = {false, false};
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        bool cxa = false, cxb = false;
+        int32_t xa = 0, xb = 0;
+        if (px[k] >= 0)
+          c24_pair_apply<EXACT>(A, Rid, t, thr, G, px[k], e[k], v[k], G.meta[pw[k]], &G.meta[pw[k]], false, 0,
+                                in_level, cross[k], cxa, xa, cxb, xb, ls);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; k++) c24_append(A, nf, false, cross[k], e[k], false, 0, false, 0);
     }
     c24_sync<BLOCK>();
     c24_flush<EXACT, BLOCK>(A, Rid, t, thr, nf, G, nc, lo, false, ls);
@@ -555,26 +604,34 @@ __device__ void c24_item(const PeelArgs& A, int32_t Rid, int sub, int nsub, uint
 }
 
 // next entry of the block queue (r-clique << 32 | sub-task << 16 | sub-tasks), or ~0 when it is
-// empty (thread 0 of a block)
+// empty for good (thread 0 of a block).  Every claim takes a ticket (one atomic add, no retries); a
+// ticket below the number of entries pushed so far names its entry, which the pusher may still be
+// writing (wait for it); a higher ticket waits until either an entry arrives for it or every
+// block has finished its warp phase (no more pushes: the queue is closed).  Every wait is bounded.
 __device__ __forceinline__ unsigned long long c24_claim(const PeelArgs& A) {
   PeelCtl* ctl = A.lk.ctl;
   volatile PeelCtl* vc = ctl;
-  for (int it = 0; it < (1 << 22); ++it) {
-    const unsigned long long k = vc->c24_hk;
-    if (k >= vc->c24_hn || vc->err) return ~0ull;
-    if (atomicCAS(&ctl->c24_hk, k, k + 1) != k) continue;
-    // the pusher reserved slot k before writing it: wait (bounded) for the entry
-    volatile unsigned long long* slot = A.c24_queue + k;
-    for (int sp = 0; sp < (1 << 24); ++sp) {
-      const unsigned long long v = *slot;
-      if (v != ~0ull) {
-        *slot = ~0ull;  // the queue is all ~0 again once every entry is taken (end of the round)
-        return v;
+  const unsigned long long k = atomicAdd(&ctl->c24_hk, 1ull);
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (vc->err) return ~0ull;
+    if (k < vc->c24_hn) {
+      volatile unsigned long long* slot = A.c24_queue + k;
+      for (int sp = 0; sp < (1 << 24); ++sp) {
+        const unsigned long long v = *slot;
+        if (v != ~0ull) {
+          *slot = ~0ull;  // the queue is all ~0 again once every entry is taken (end of the round)
+          return v;
+        }
+        __nanosleep(32);
       }
-      __nanosleep(32);
+      break;
     }
-    atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
-    return ~0ull;
+    if (vc->c24_done == gridDim.x) {
+      __threadfence();
+      if (k >= vc->c24_hn) return ~0ull;  // closed, and nothing left for this ticket
+      continue;
+    }
+    __nanosleep(64);
   }
   atomicCAS(&ctl->err, 0, NH_ERR_TIMEOUT);
   return ~0ull;
@@ -588,8 +645,12 @@ __device__ __forceinline__ unsigned long long c24_claim(const PeelArgs& A) {
 // c24_len_mult times the list length (each sub-task stages the whole list); s_pref[i] = K_0 + ... + K_i.  Returns the number of sub-tasks; n > kTaskItems:
 // one per r-clique (s_pref unused).
 __device__ __forceinline__ unsigned long long c24_prefix(const PeelArgs& A, const int32_t* items, unsigned long long n,
-                                                         long long nwarps, uint32_t* s_pref, unsigned long long* s_red) {
-  if (n > (unsigned long long)kTaskItems) return n;
+                                                         long long nwarps, uint32_t* s_pref, unsigned long long* s_red,
+                                                         int* any_long) {
+  if (n > (unsigned long long)kTaskItems) {
+    *any_long = 1;  // not looked at: the block queue phase runs
+    return n;
+  }
   constexpr int kPer = kTaskItems / kThreads;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned int b = threadIdx.x * kPer;
@@ -607,14 +668,25 @@ __device__ __forceinline__ unsigned long long c24_prefix(const PeelArgs& A, cons
     }
     sum += est[j];
   }
+  bool lng = false;
+#pragma unroll
+  for (int j = 0; j < kPer; j++) lng = lng || len[j] > (uint32_t)kC24WarpCap;
   sum = warp_sum_u64(sum);
-  __syncthreads();  // the previous round's readers of s_pref / s_red are done
+  lng = __any_sync(NH_FULL, lng);
+  __syncthreads();  // the previous round's readers of s_pref / s_red / any_long are done
+  if (threadIdx.x == 0) *any_long = 0;
+  __syncthreads();
   if (lane == 0) s_red[wib] = sum;
+  if (lane == 0 && lng) *any_long = 1;
   __syncthreads();
   unsigned long long W = 0;
   for (int w = 0; w < kThreads / 32; w++) W += s_red[w];
   if (W == 0) W = 1;
-  const double q = (double)A.c24_per_warp * (double)nwarps / (double)W;  // warp sub-tasks per unit of scan bound
+  // single precision on purpose: this runs every round in every block, and only the schedule
+  // depends on it
+  const float q = A.c24_per_warp * (float)nwarps / (float)W;  // warp sub-tasks per unit of scan bound
+  const float qb = q * (1.0f / (kThreads / 32));
+  const float rw = 1.0f / (float)A.c24_wgrain, rb = 1.0f / (float)A.c24_bgrain;
   uint32_t k[kPer];
   unsigned long long ks = 0;
 #pragma unroll
@@ -622,14 +694,16 @@ __device__ __forceinline__ unsigned long long c24_prefix(const PeelArgs& A, cons
     k[j] = 0;
     if (b + j < n) {
       const bool blk = len[j] > (uint32_t)kC24WarpCap;
-      const double want = blk ? q * (double)est[j] / (kThreads / 32) : q * (double)est[j];
-      double grain = blk ? (double)A.c24_bgrain : (double)A.c24_wgrain;
-      const double lg = (double)A.c24_len_mult * (double)len[j];
-      if (lg > grain) grain = lg;
-      const double most = (double)est[j] / grain + 1.0;
-      double kk = want < most ? want : most;
-      if (kk > (double)kC24MaxSplit) kk = (double)kC24MaxSplit;
-      k[j] = kk < 1.0 ? 1u : (uint32_t)kk;
+      const float e = (float)est[j];
+      const float want = (blk ? qb : q) * e;
+      float most = e * (blk ? rb : rw) + 1.0f;
+      if (A.c24_len_mult > 0) {
+        const float m2 = __fdividef(e, (float)A.c24_len_mult * (float)len[j]) + 1.0f;
+        most = m2 < most ? m2 : most;
+      }
+      float kk = want < most ? want : most;
+      kk = kk < (float)kC24MaxSplit ? kk : (float)kC24MaxSplit;
+      k[j] = kk < 1.0f ? 1u : (uint32_t)kk;
     }
     ks += k[j];
   }
@@ -659,7 +733,7 @@ __device__ __forceinline__ unsigned long long c24_prefix(const PeelArgs& A, cons
 // Re-lists the n r-cliques of items (frontier or level), block-collective.  smem: kC24SmemBytes.
 template <bool EXACT>
 __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long long n, uint32_t t, uint32_t thr,
-                         int32_t* nf, long long nwarps, unsigned char* smem, LocalStats& ls) {
+                         int32_t* nf, long long gwarp, long long nwarps, unsigned char* smem, LocalStats& ls) {
   PeelCtl* ctl = A.lk.ctl;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -672,18 +746,34 @@ __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long 
   const C24Area Gw = c24_area(smem + (size_t)kC24WarpBytes * wib, kC24WarpHS, 9, kC24WarpCap);
   const C24Area Gb = c24_area(smem, kC24BlockHS, 12, kC24BlockCap);
   const bool split = n <= (unsigned long long)kTaskItems;
-  const unsigned long long ntask = c24_prefix(A, items, n, nwarps, s_pref, s_red);
+  const unsigned long long ntask = c24_prefix(A, items, n, nwarps, s_pref, s_red, tcnt + 9);
+  const bool any_long = tcnt[9] != 0;  // every block computed the same
+  const bool trace = A.round_log && !A.union_mode && blockIdx.x == 0 && threadIdx.x == 0 && t >= 1 &&
+                     t <= A.round_log_cap;  // block 0's phase times of the round
+  if (trace) A.round_log[8 * (t - 1) + 5] = nh_globaltimer();
   const unsigned long long expand0 = ls.expand;
   if (A.round_log && blockIdx.x == 0 && threadIdx.x == 0) ctl->c24_tasks = ntask;
-  // warps: sub-tasks in batches from a shared counter
-  const unsigned long long per = ntask / ((unsigned long long)nwarps * 8ull);
+  // warps: sub-task gwarp first (no counter traffic when a round has fewer sub-tasks than warps),
+  // then the rest, from nwarps on, in batches from a shared counter
+  const unsigned long long NW = (unsigned long long)nwarps;
+  const unsigned long long rest = ntask > NW ? ntask - NW : 0ull;
+  const unsigned long long per = rest / (NW * 8ull);
   const unsigned long long bt = per > 0 ? per : 1ull;
+  bool first = true;
   for (;;) {
-    unsigned long long k0 = 0;
-    if (lane == 0) k0 = atomicAdd(&ctl->c24_next, bt);
-    k0 = __shfl_sync(NH_FULL, k0, 0);
+    unsigned long long k0 = 0, k1 = 0;
+    if (first) {
+      first = false;
+      k0 = (unsigned long long)gwarp;
+      k1 = k0 + 1;
+    } else {
+      if (rest == 0) break;
+      if (lane == 0) k0 = atomicAdd(&ctl->c24_next, bt);
+      k0 = NW + __shfl_sync(NH_FULL, k0, 0);
+      k1 = k0 + bt;
+    }
     if (k0 >= ntask) break;
-    const unsigned long long k1 = k0 + bt < ntask ? k0 + bt : ntask;
+    if (k1 > ntask) k1 = ntask;
     for (unsigned long long k = k0; k < k1; ++k) {
       unsigned int i = (unsigned int)k;
       int sub = 0, nsub = 1;
@@ -717,9 +807,16 @@ __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long 
       if (len > 0) c24_item<EXACT, false>(A, Rid, sub, nsub, t, thr, nf, Gw, wacc, tcnt + wib, nullptr, nullptr, ls);
     }
   }
-  // blocks: the long lists
-  __syncthreads();
-  for (;;) {
+  if (trace) A.round_log[8 * (t - 1) + 6] = nh_globaltimer();
+  // blocks: the long lists (none in this round: skip the queue)
+  if (any_long) {
+    __syncthreads();  // this block's warps have pushed everything they will push this round
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&ctl->c24_done, 1u);
+    }
+  }
+  while (any_long) {
     if (threadIdx.x == 0) *bcast = c24_claim(A);
     __syncthreads();
     const unsigned long long e = *bcast;
@@ -728,6 +825,7 @@ __device__ void c24_list(const PeelArgs& A, const int32_t* items, unsigned long 
     c24_item<EXACT, true>(A, (int32_t)(e >> 32), (int)((e >> 16) & 0xffffu), (int)(e & 0xffffu), t, thr, nf, Gb,
                           wacc, tcnt + 8, wcnt, s_red, ls);
   }
+  if (trace) A.round_log[8 * (t - 1) + 7] = nh_globaltimer();
   if (A.round_log) {
     const unsigned long long d = warp_sum_u64(ls.expand - expand0);
     if (lane == 0 && d) atomicAdd(&ctl->dbg_work, d);

@@ -417,14 +417,16 @@ def set_relist_split(per_warp: float = 1.0, warp_grain: int = 128, block_grain: 
 
 
 def debug_round_log(log: torch.Tensor | None):
-    """Trace the rounds of the next peels into log (int64 device tensor of 4*cap entries): per
+    """Trace the rounds of the next peels into log (int64 device tensor of 8*cap entries): per
     round (frontier size << 32 | levels opened so far, device timer in ns at the round's end,
-    out-list entries expanded, sub-tasks << 32 | block sub-tasks); None turns the trace off."""
+    out-list entries expanded, sub-tasks << 32 | block sub-tasks, then block 0's timer at the
+    (2,4) re-listing's start, after its split, after its warp phase, at its end); None turns the
+    trace off."""
     if log is None:
         _check("nh_debug_round_log", lib().nh_debug_round_log(None, 0))
     else:
         assert log.dtype == torch.int64 and log.is_cuda
-        _check("nh_debug_round_log", lib().nh_debug_round_log(_dptr(log), log.numel() // 4))
+        _check("nh_debug_round_log", lib().nh_debug_round_log(_dptr(log), log.numel() // 8))
 
 
 def _cuda_timer(run) -> float:
