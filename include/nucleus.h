@@ -257,13 +257,18 @@ int nh_set_peel_max_group(int g);
  * n in [-1, 4096]; NH_ERR_INVALID otherwise.  Results never depend on it. */
 int nh_set_peel_task_items(int n);
 
-/* Tuning knob (process-wide, default 1): with on = 1 the (2,4) peel without links (link mode 2,
- * the approximate peel) and the (2,4) two-phase / label hierarchies re-list each edge from its
- * triangle list (built by nh_index_r_cliques for r = 2): candidates whose edges to the frontier
- * edge were peeled earlier (or, in the hierarchy, lie below the level) are dropped before any
- * pair is formed, the rest are staged in shared memory, and the decrements of one candidate's two
- * edges are summed.  on = 0 uses the adjacency-scan re-listing of every other pair.  Results never
- * depend on it.  NH_ERR_INVALID for other values. */
+/* Tuning knob (process-wide, default 1): with on = 1
+ *  - the (2,4) peel without links (link mode 2, the approximate peel) and the (2,4) two-phase /
+ *    label hierarchies re-list each edge from its triangle list (built by nh_index_r_cliques for
+ *    r = 2): candidates whose edges to the frontier edge were peeled earlier (or, in the
+ *    hierarchy, lie below the level) are dropped before any pair is formed, the rest are staged
+ *    in shared memory, and the decrements of one candidate's two edges are summed;
+ *  - every (3,4) peel and hierarchy re-lists over a copy of the per-edge triangle lists whose
+ *    entries also carry their triangle's round stamp and value (16 bytes per entry, 48 bytes per
+ *    triangle of working memory for the call), so that a list search returns all a 4-clique's
+ *    member needs in one read.
+ * on = 0 uses the plain re-listing of every other pair.  Results never depend on it.
+ * NH_ERR_INVALID for other values. */
 int nh_set_peel_relist24(int on);
 
 /* Tuning knob of that (2,4) re-listing (process-wide): a frontier (or level) of at most 4096

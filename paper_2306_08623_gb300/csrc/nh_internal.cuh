@@ -8,6 +8,7 @@
 //   uoff[n+1] (i64) first lexicographic edge id of each vertex (edges (u,v), u<v)
 //   eu[m], ev[m]    endpoints of edge id e (eu < ev)
 //   tri[3 n_r]      vertices of triangle id t (r = 3), toff[m+1] (i64) first triangle id per edge
+//   tedge[3 n_r]    ids of the edges {a,b}, {a,c}, {b,c} of triangle t = {a < b < c}
 //   table[cap]      16-byte slots {key u64, id u32, pad}: key = (edge id of (a,b)) << 32 | c
 //   ekey[cap] (u64), eval[cap]   open-addressing edge table (load <= 0.5): key (u << 32 | v), u < v,
 //                   and the edge id in the parallel value array (a miss reads the 8-byte keys only,
@@ -59,6 +60,7 @@ struct nh_rindex {
   int64_t n_r;
   const nh_oriented* o;
   int32_t* tri;
+  int32_t* tedge;
   int64_t* toff;
   nh_slot* table;
   unsigned long long mask;
@@ -88,6 +90,7 @@ struct GView {
   const uint32_t* eval;
   unsigned long long emask;
   const int32_t* tri;
+  const int32_t* tedge;
   const nh_slot* table;
   unsigned long long mask;
   const int64_t* etoff;
@@ -108,6 +111,7 @@ static inline GView make_view(const nh_oriented* o, const nh_rindex* ri) {
   g.eu = o->eu; g.ev = o->ev;
   g.ekey = o->ekey; g.eval = o->eval; g.emask = o->emask;
   g.tri = ri ? ri->tri : nullptr;
+  g.tedge = ri ? ri->tedge : nullptr;
   g.table = ri ? ri->table : nullptr;
   g.mask = ri ? ri->mask : 0ull;
   g.etoff = ri ? ri->etoff : nullptr;

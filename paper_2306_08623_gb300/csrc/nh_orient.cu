@@ -133,9 +133,10 @@ __global__ void k_tri_count(int64_t m, const int64_t* __restrict__ off, const in
 }
 
 __global__ void k_tri_fill(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                           const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                           const int64_t* __restrict__ toff, int32_t* __restrict__ tri, nh_slot* __restrict__ table,
-                           unsigned long long mask, int* __restrict__ status) {
+                           const int32_t* __restrict__ eid, const int32_t* __restrict__ eu,
+                           const int32_t* __restrict__ ev, const int64_t* __restrict__ toff, int32_t* __restrict__ tri,
+                           int32_t* __restrict__ tedge, nh_slot* __restrict__ table, unsigned long long mask,
+                           int* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -143,7 +144,8 @@ __global__ void k_tri_fill(int64_t m, const int64_t* __restrict__ off, const int
     const int32_t a = eu[e], b = ev[e];
     int64_t ab = nh_lower_bound(adj, off[a], off[a + 1], b + 1), ae = off[a + 1];
     int64_t bb = nh_lower_bound(adj, off[b], off[b + 1], b + 1), be = off[b + 1];
-    if (ae - ab > be - bb) {
+    const bool scan_a = ae - ab <= be - bb;
+    if (!scan_a) {
       int64_t t0 = ab, t1 = ae;
       ab = bb; ae = be; bb = t0; be = t1;
     }
@@ -151,17 +153,21 @@ __global__ void k_tri_fill(int64_t m, const int64_t* __restrict__ off, const int
     for (int64_t base = ab; base < ae; base += 32) {
       const int64_t j = base + lane;
       int32_t c = 0;
-      bool hit = false;
+      int64_t q = -1;
       if (j < ae) {
         c = adj[j];
-        hit = nh_find(adj, bb, be, c) >= 0;
+        q = nh_find(adj, bb, be, c);
       }
+      const bool hit = q >= 0;
       const unsigned msk = __ballot_sync(NH_FULL, hit);
       if (hit) {
         const int64_t id = pos + __popc(msk & ((1u << lane) - 1u));
         tri[3 * id + 0] = a;
         tri[3 * id + 1] = b;
         tri[3 * id + 2] = c;
+        tedge[3 * id + 0] = (int32_t)e;                 // {a, b}
+        tedge[3 * id + 1] = eid[scan_a ? j : q];         // {a, c}
+        tedge[3 * id + 2] = eid[scan_a ? q : j];         // {b, c}
         const unsigned long long key = ((unsigned long long)(uint32_t)e << 32) | (uint32_t)c;
         unsigned long long h = nh_mix64(key) & mask;
         bool done = false;
@@ -359,7 +365,7 @@ void free_oriented(nh_oriented* o) {
 
 void free_rindex(nh_rindex* ri) {
   if (!ri) return;
-  cudaFree(ri->tri); cudaFree(ri->toff); cudaFree(ri->table);
+  cudaFree(ri->tri); cudaFree(ri->tedge); cudaFree(ri->toff); cudaFree(ri->table);
   cudaFree(ri->etoff); cudaFree(ri->etw); cudaFree(ri->ettid);
   cudaFree(ri->t2off); cudaFree(ri->t2w); cudaFree(ri->t2ea); cudaFree(ri->t2eb); cudaFree(ri->t2cost);
   delete ri;
@@ -556,6 +562,7 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
     while (cap < 2ull * (unsigned long long)ntri) cap <<= 1;
     if (g_nh_inject_table_cap > 0) cap = (unsigned long long)g_nh_inject_table_cap;
     if (!rc) rc = nh_alloc(&ri->tri, 3 * ntri, st);
+    if (!rc) rc = nh_alloc(&ri->tedge, 3 * ntri, st);
     if (!rc) rc = nh_alloc(&ri->table, (int64_t)cap, st);
     if (!rc) {
       ri->mask = cap - 1;
@@ -563,8 +570,8 @@ extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, 
       cudaMemsetAsync(status, 0, sizeof(int), st);
       k_fill_empty<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(ri->table, cap);
       nh_note_launch();
-      k_tri_fill<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eu, o->ev, ri->toff, ri->tri, ri->table,
-                                                     ri->mask, status);
+      k_tri_fill<<<warp_grid(m), kThreads, 0, st>>>(m, o->off, o->adj, o->eid, o->eu, o->ev, ri->toff, ri->tri,
+                                                     ri->tedge, ri->table, ri->mask, status);
     nh_note_launch();
       int hs = 0;
       cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -49,6 +49,26 @@ __global__ void k_peel_init(int64_t n_r, const uint32_t* __restrict__ cnt0, uint
   }
 }
 
+// (3,4) mirrored lists: entry k of edge e's triangle list = {w, triangle, stamp, value} with
+// stamp = value = init (the value array's entry when init is given, else 0), and the list
+// position of every triangle's three entries (slot = which of its edges the list belongs to)
+__global__ void k_et3_fill(GView g, int4* __restrict__ et3, int32_t* __restrict__ tpos,
+                           const uint32_t* __restrict__ init) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < g.m; e += nwarps) {
+    for (int64_t k = g.etoff[e] + lane; k < g.etoff[e + 1]; k += 32) {
+      const int32_t tid = g.ettid[k];
+      const int32_t* te = g.tedge + 3 * (int64_t)tid;
+      const int slot = (te[0] == (int32_t)e) ? 0 : (te[1] == (int32_t)e) ? 1 : 2;
+      tpos[3 * (int64_t)tid + slot] = (int32_t)k;
+      const int32_t v = init ? (int32_t)init[tid] : 0;
+      et3[k] = make_int4(g.etw[k], tid, v, v);
+    }
+  }
+}
+
 __global__ void k_peel_result(const PeelCtl* c, int64_t* res) {
   if (res[0] == 0) res[0] = c->err ? c->err : (c->done ? NH_OK : NH_ERR_INTERNAL);
   res[3] = (int64_t)c->st_rounds;
@@ -194,6 +214,16 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   }
   if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
+  if (r == 3 && s == 4 && g_peel_relist24 && A.g.tedge && 3 * n_r < (1ll << 31)) {
+    if (nh_alloc(&A.et3, 3 * n_r, st) == NH_OK && nh_alloc(&A.tpos, 3 * n_r, st) == NH_OK) {
+      k_et3_fill<<<nh_blocks_for(A.g.m * 32, 256, 152 * 16), 256, 0, st>>>(A.g, A.et3, A.tpos, nullptr);
+      nh_note_launch();
+    } else {  // no room: the plain lists
+      (void)cudaGetLastError();
+      nh_free(A.et3, st); nh_free(A.tpos, st);
+      A.et3 = nullptr; A.tpos = nullptr;
+    }
+  }
   if (exact) {
     if ((rc = nh_alloc(&A.lk.ovf[0], (int64_t)A.lk.ovf_cap, st)) || (rc = nh_alloc(&A.lk.ovf[1], (int64_t)A.lk.ovf_cap, st)))
       goto cleanup;
@@ -268,6 +298,7 @@ cleanup:
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
   nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
   nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st); nh_free(A.c24_queue, st);
+  nh_free(A.et3, st); nh_free(A.tpos, st);
   if (res_dev) return (cudaGetLastError() != cudaSuccess && !rc) ? NH_ERR_CUDA : rc;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
@@ -440,6 +471,16 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   if (A.use24) cudaMemsetAsync(A.c24_queue, 0xff, sizeof(unsigned long long) * A.c24_qcap, st);
   if ((rc = chunk_cost_pair(r, s, A.g, n_r, cost, st))) goto cleanup;
   A.cost = cost;
+  if (r == 3 && s == 4 && g_peel_relist24 && A.g.tedge && 3 * n_r < (1ll << 31)) {
+    if (nh_alloc(&A.et3, 3 * n_r, st) == NH_OK && nh_alloc(&A.tpos, 3 * n_r, st) == NH_OK) {
+      k_et3_fill<<<nh_blocks_for(A.g.m * 32, 256, 152 * 16), 256, 0, st>>>(A.g, A.et3, A.tpos, core);
+      nh_note_launch();
+    } else {
+      (void)cudaGetLastError();
+      nh_free(A.et3, st); nh_free(A.tpos, st);
+      A.et3 = nullptr; A.tpos = nullptr;
+    }
+  }
   cudaMemsetAsync(dmax, 0, sizeof(unsigned int), st);
   k_max_u32<<<nh_blocks_for(n_r, 256, 152 * 8), 256, 0, st>>>(n_r, core, dmax);
   nh_note_launch();
@@ -481,7 +522,7 @@ cleanup:
   nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
   nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
   nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(cost, st);
-  nh_free(mark, st); nh_free(A.c24_queue, st);
+  nh_free(mark, st); nh_free(A.c24_queue, st); nh_free(A.et3, st); nh_free(A.tpos, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }

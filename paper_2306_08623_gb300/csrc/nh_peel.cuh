@@ -90,6 +90,8 @@ struct PeelArgs {
   int stats;
   unsigned long long timeout_ns;
   int use24;              // (2,4) without links: re-list over the per-edge triangle lists
+  int4* et3;              // (3,4): per-edge triangle lists with mirrored state, {w, triangle, stamp, value}
+  int32_t* tpos;          //        the three list positions of every triangle (or null: plain lists)
   unsigned long long* round_log;  // optional trace: per round (frontier << 32 | levels, end time)
   unsigned long long round_log_cap;
   unsigned long long* c24_queue;  // block queue of that re-listing (all ~0 between rounds)
@@ -378,6 +380,17 @@ static __device__ __noinline__ LinkDelta link_run_call(const LinkEnv E, int32_t 
 // per (R, S) step
 // ---------------------------------------------------------------------------------------------
 
+// (3,4) with mirrored lists: triangle x's round stamp and value, copied into its three list
+// entries (8-byte stores: a reader of an entry sees the pair before or after, never half of it)
+__device__ __forceinline__ void mirror_set(const PeelArgs& A, int32_t x, uint32_t rd, uint32_t v) {
+  const int32_t* tp = A.tpos + 3 * (int64_t)x;
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int64_t k = __ldg(tp + j);
+    __stcg(reinterpret_cast<uint2*>(reinterpret_cast<char*>(A.et3 + k) + 8), make_uint2(rd, v));
+  }
+}
+
 template <bool EXACT>
 __device__ __forceinline__ void dec(const PeelArgs& A, int32_t x, uint32_t t, uint32_t thr, int32_t* nf,
                                     LocalStats& ls) {
@@ -386,8 +399,10 @@ __device__ __forceinline__ void dec(const PeelArgs& A, int32_t x, uint32_t t, ui
   if (old == thr + 1u) {
     const unsigned long long pos = atomicAdd(&A.lk.ctl->nf_count, 1ull);
     nf[pos] = x;
+    const uint32_t v = EXACT ? thr : min(thr, __ldg(A.cnt0 + x));
     __stcg(A.round + x, t + 1u);
-    __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
+    __stcg(A.val + x, v);
+    if (A.et3) mirror_set(A, x, t + 1u, v);
   }
 }
 
@@ -584,6 +599,73 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
   }
 }
 
+// process_S with the members' round stamps rdv (peel) and values cv (core or approximate value)
+// already loaded (the (3,4) mirrored lists); the same decisions as process_S
+template <int CM, bool EXACT>
+__device__ __forceinline__ void process_S_pre(const PeelArgs& A, int32_t Rid, const int32_t (&mem)[CM],
+                                              const uint32_t (&rdv)[CM], const uint32_t (&cv)[CM], uint32_t t,
+                                              uint32_t thr, int32_t* nf, const WarpLinks& W, LocalStats& ls) {
+  ls.stamp += CM;
+  if (A.union_mode) {
+    int32_t attr = Rid;
+#pragma unroll
+    for (int j = 0; j < CM; j++) {
+      if (cv[j] < thr) return;
+      if (cv[j] == thr && mem[j] < attr) attr = mem[j];
+    }
+    ls.listed++;
+    if (A.mark && !__ldcg(A.mark + Rid)) __stcg(A.mark + Rid, 1u);
+    if (attr != Rid) return;
+#pragma unroll
+    for (int j = 0; j < CM; j++) {
+      const int32_t child = uf_unite(A.lk.uf, Rid, mem[j], A.lk.ctl);
+      if (child >= 0) {
+        ls.unite++;
+        const unsigned long long pos = atomicAdd(A.touched_n, 2ull);
+        if (pos + 1 < A.touched_cap) {
+          A.touched[pos] = child;
+          A.touched[pos + 1] = uf_find(A.lk.uf, child);
+        } else {
+          atomicCAS(&A.lk.ctl->err, 0, NH_ERR_OVERFLOW);
+        }
+      }
+    }
+    return;
+  }
+  bool dead = false;
+  int32_t attr = Rid;
+#pragma unroll
+  for (int j = 0; j < CM; j++) {
+    if (rdv[j] != 0u && rdv[j] < t) dead = true;
+    else if (rdv[j] == t && mem[j] < attr) attr = mem[j];
+  }
+  ls.listed++;
+  if (dead) {
+    if (EXACT && A.link_mode == 0) {
+      int32_t best = -1;
+      uint32_t bc = kNone;
+#pragma unroll
+      for (int j = 0; j < CM; j++)
+        if (rdv[j] != 0u && rdv[j] < t && cv[j] < bc) { bc = cv[j]; best = mem[j]; }
+      wl_add(W, A, Rid, best, ls);
+    }
+  } else if (attr == Rid) {
+#pragma unroll
+    for (int j = 0; j < CM; j++)
+      if (rdv[j] == 0u || rdv[j] > t) dec<EXACT>(A, mem[j], t, thr, nf, ls);
+    if (EXACT && A.link_mode == 0) {
+#pragma unroll
+      for (int j = 0; j < CM; j++)
+        if (rdv[j] == t) wl_add(W, A, Rid, mem[j], ls);
+    }
+  }
+  if (EXACT && A.link_mode == 1) {
+#pragma unroll
+    for (int j = 0; j < CM; j++)
+      if (rdv[j] != 0u && rdv[j] <= t) wl_add(W, A, Rid, mem[j], ls);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // re-listing of one frontier r-clique by one warp
 // ---------------------------------------------------------------------------------------------
@@ -593,6 +675,13 @@ __device__ __forceinline__ void process_S(const PeelArgs& A, int32_t Rid, const 
 // round or is in the frontier with a smaller id (peel), or when x lies below the level or is of
 // the level with a smaller id (two-phase hierarchy; the label hierarchy keeps the latter, whose
 // s-cliques still mark R).  process_S decides exactly; this only saves the searches for the rest.
+__device__ __forceinline__ bool member_may_count_v(const PeelArgs& A, int32_t Rid, int32_t x, uint32_t rd, uint32_t c,
+                                                   uint32_t t, uint32_t thr) {
+  if (A.union_mode) return c >= thr && (A.mark || c > thr || x > Rid);
+  if (A.link_mode == 0 || A.link_mode == 1) return true;
+  return !((rd != 0u && rd < t) || (rd == t && x < Rid));
+}
+
 __device__ __forceinline__ bool member_may_count(const PeelArgs& A, int32_t Rid, int32_t x, uint32_t t, uint32_t thr,
                                                  LocalStats& ls) {
   if (A.union_mode) {
@@ -675,10 +764,14 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
     vx[2] = __ldg(g.tri + 3 * (int64_t)Rid + 2);
     int32_t mine = 0;
     if (lane < 3) {
-      const int32_t x = (lane == 2) ? vx[1] : vx[0];
-      const int32_t y = (lane == 0) ? vx[1] : vx[2];
-      const int64_t p = nh_find(g.adj, __ldg(g.off + x), __ldg(g.off + x + 1), y);
-      mine = (p >= 0) ? __ldg(g.eid + p) : 0;
+      if (g.tedge) {
+        mine = __ldg(g.tedge + 3 * (int64_t)Rid + lane);
+      } else {
+        const int32_t x = (lane == 2) ? vx[1] : vx[0];
+        const int32_t y = (lane == 0) ? vx[1] : vx[2];
+        const int64_t p = nh_find(g.adj, __ldg(g.off + x), __ldg(g.off + x + 1), y);
+        mine = (p >= 0) ? __ldg(g.eid + p) : 0;
+      }
     }
     eR[0] = __shfl_sync(NH_FULL, mine, 0);
     eR[1] = __shfl_sync(NH_FULL, mine, 1);
@@ -696,6 +789,52 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
     int bt = 0;
     if (th[1] - tl[1] < th[bt] - tl[bt]) bt = 1;
     if (th[2] - tl[2] < th[bt] - tl[bt]) bt = 2;
+    if (A.et3) {
+      // mirrored lists: an entry holds its triangle's round stamp and value, so a search hit
+      // brings everything the s-clique needs in one sector
+      if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(4 * (th[bt] - tl[bt]));
+      for (int64_t c = c0; c < cend && tl[bt] + 32 * c < th[bt]; c += cstep) {
+        const int64_t j = tl[bt] + 32 * c + lane;
+        bool ok = j < th[bt];
+        int32_t mem[3] = {0, 0, 0};
+        uint32_t rdv[3] = {0, 0, 0}, cv[3] = {0, 0, 0};
+        if (ok) {
+          const int4 en = __ldcg(A.et3 + j);
+          const int32_t w = en.x;
+          mem[bt] = en.y;
+          rdv[bt] = (uint32_t)en.z;
+          cv[bt] = (uint32_t)en.w;
+          ok = member_may_count_v(A, Rid, en.y, rdv[bt], cv[bt], t, thr);
+#pragma unroll
+          for (int i = 0; i < 3; i++) {
+            if (i != bt && ok) {
+              int64_t lo = tl[i], hi = th[i];  // first entry with w' >= w
+              while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (__ldg(reinterpret_cast<const int32_t*>(A.et3 + mid)) < w) lo = mid + 1; else hi = mid;
+              }
+              ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps
+              if (lo < th[i]) {
+                const int4 f = __ldcg(A.et3 + lo);
+                if (f.x == w) {
+                  mem[i] = f.y;
+                  rdv[i] = (uint32_t)f.z;
+                  cv[i] = (uint32_t)f.w;
+                  ls.scan += 3;
+                } else {
+                  ok = false;
+                }
+              } else {
+                ok = false;
+              }
+            }
+          }
+        }
+        if (ok) process_S_pre<3, EXACT>(A, Rid, mem, rdv, cv, t, thr, nf, W, ls);
+        if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
+      }
+      return;
+    }
     if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(th[bt] - tl[bt]);
     for (int64_t c = c0; c < cend && tl[bt] + 32 * c < th[bt]; c += cstep) {
       const int64_t j = tl[bt] + 32 * c + lane;
@@ -1168,8 +1307,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks<R, S>()) k_peel(PeelArgs 
           const unsigned long long pos = warp_append(&ctl->f_count, take, lane);
           if (take) {
             fr[pos] = x;
+            const uint32_t v = EXACT ? thr : min(thr, __ldg(A.cnt0 + x));
             __stcg(A.round + x, t);
-            __stcg(A.val + x, EXACT ? thr : min(thr, __ldg(A.cnt0 + x)));
+            __stcg(A.val + x, v);
+            if constexpr (R == 3 && S == 4) {
+              if (A.et3) mirror_set(A, x, t, v);
+            }
           }
         }
       }

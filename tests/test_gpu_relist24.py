@@ -1,6 +1,7 @@
 """The (2,4) re-listing over per-edge triangle lists (warp-staged, block-staged and multi-slab
-candidate sets) and the (2,3) re-listing over the same lists, against the oracle and against the
-adjacency-scan re-listing (nh_set_peel_relist24(0)), through the C-ABI.
+candidate sets), the (2,3) re-listing over the same lists and the (3,4) re-listing over the
+mirrored triangle lists, against the oracle and against the plain re-listing
+(nh_set_peel_relist24(0)), through the C-ABI.
 
 Graphs with hub edges whose triangle lists are longer than a warp's staging area (512) and than
 a block's (4096) drive every branch; the exact core numbers and round stamps, the two-phase
@@ -46,6 +47,9 @@ def _run(nc, off, adj, r, s, on):
         parent, label, nn = nc.hierarchy_two_phase(o, ri, s, pk["core"])
         out = {"n_s": n_s, "cnt": u32(cnt), "core": u32(pk["core"]), "round": u32(pk["round"]),
                "parent": parent.cpu().numpy(), "label": u32(label), "nn": nn, "stats": pk["stats"]}
+        el = nc.peel_and_link(o, ri, s, cnt)  # the linking peel (the (3,4) builder of the benchmark)
+        ep, elab, enn = nc.construct_tree(el["core"], el["uf"], el["L"])
+        out["el"] = (u32(el["core"]), ep.cpu().numpy(), u32(elab), enn)
         for d in (0.1, 0.5):
             a = nc.approx_nucleus(o, ri, s, d, cnt, stats=True)
             out["approx_%g" % d] = u32(a["approx"])
@@ -59,7 +63,7 @@ def _run(nc, off, adj, r, s, on):
 
 
 @pytest.mark.parametrize("name", sorted(GRAPHS))
-@pytest.mark.parametrize("r,s", [(2, 4), (2, 3)])
+@pytest.mark.parametrize("r,s", [(2, 4), (2, 3), (3, 4)])
 def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     off, adj = GRAPHS[name]()
     ref = oracle.nucleus(off, adj, r, s)
@@ -68,6 +72,9 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     assert np.array_equal(g["cnt"], ref["cnt"])
     assert np.array_equal(g["core"], ref["core"])
     compare_hierarchy(g["parent"], g["label"], g["nn"], ref["leaf_node"], ref["node_parent"], ref["node_label"])
+    ec, ep, elab, enn = g["el"]
+    assert np.array_equal(ec, ref["core"])
+    compare_hierarchy(ep, elab, enn, ref["leaf_node"], ref["node_parent"], ref["node_label"])
     for d in (0.1, 0.5):
         ra = oracle.nucleus(off, adj, r, s, hier=None, approx_delta=d)
         assert np.array_equal(g["approx_%g" % d], ra["approx"]), d
