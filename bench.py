@@ -632,13 +632,11 @@ def measure_batch512(warmup: int = 0, steps: int = 1) -> dict:
     graphs = [gg.batch_member(1000 + i) for i in range(n_graphs)]
     dev = [(torch.from_numpy(o).cuda(), torch.from_numpy(a).cuda()) for o, a in graphs]
     tot_m = sum(len(a) // 2 for _, a in graphs)
-    off_u, adj_u, vbase = nc.batch_union(dev)
-    o_u = nc.build_orientation(off_u, adj_u)
-    ri23 = nc.index_r_cliques(o_u, 2)
-    buf23 = nc.hierarchy_buffers(ri23)
-    tuned = nc.autotune_peel(lambda: nc.hierarchy_enqueue(o_u, ri23, 3, buf23), max_groups=(64, 1024),
+    b23 = nc.Batch(dev, 2)
+    buf23 = b23.buffers()
+    tuned = nc.autotune_peel(lambda: b23.run(3, buf23), max_groups=(64, 1024),
                              task_items=(0, -1))
-    del buf23, ri23, o_u
+    del buf23, b23
     res = {}
     for r, s in [(2, 3), (3, 4)]:
         t_one, t_batch = [], []
@@ -654,13 +652,11 @@ def measure_batch512(warmup: int = 0, steps: int = 1) -> dict:
             if it < warmup + steps - 1:
                 del outs
             a = _ev()
-            off_u, adj_u, vb = nc.batch_union(dev)
-            o_u = nc.build_orientation(off_u, adj_u)
-            ri = nc.index_r_cliques(o_u, r)
-            buf = nc.hierarchy_buffers(ri)
+            bt = nc.Batch(dev, r)  # nh_batch_prepare: union, orientation, r-clique index
+            buf = bt.buffers()
             b = _ev()
             t_prep = _ms(a, b)
-            g = nc.capture_hierarchy(o_u, ri, s, buf)  # one eager run, then the capture (not timed)
+            g = bt.capture(s, buf)  # nh_batch_run: one eager run, then the capture (not timed)
             for t in buf.values():
                 t.fill_(-1)
             c = _ev()
@@ -671,8 +667,8 @@ def measure_batch512(warmup: int = 0, steps: int = 1) -> dict:
             assert status[0] == 0, status
         # every graph's slice of the union equals its own run: core numbers, and the hierarchy up to
         # node numbering (the one-by-one trees laid side by side, node ids shifted per graph)
-        rb = nc.rindex_bases(ri, vb)
-        n_r = ri.n_r
+        rb = bt.rbase
+        n_r = bt.n_r
         nn_u = int(status[2])
         assert [int(rb[i + 1] - rb[i]) for i in range(n_graphs)] == [o["n_r"] for o in outs]
         core_b = torch.cat([o["core"] for o in outs])
@@ -687,15 +683,16 @@ def measure_batch512(warmup: int = 0, steps: int = 1) -> dict:
         assert same, "the batched hierarchies differ from the one-by-one ones"
         res["%d,%d" % (r, s)] = {"n_s": int(status[1]), "one_by_one_ms": _spread(t_one[warmup:]),
                                  "batched_ms": _spread(t_batch[warmup:]), "graphs_identical": n_graphs}
-        del buf, g, ri, o_u, off_u, adj_u, outs, core_b, leaf_b, node_b, label_b
+        del buf, g, bt, outs, core_b, leaf_b, node_b, label_b
         torch.cuda.empty_cache()
     tot_one = sum(v["one_by_one_ms"]["median"] for v in res.values())
     tot_b = sum(v["batched_ms"]["median"] for v in res.values())
     return {"metric": "512-graph exact hierarchy batch time", "unit": "ms",
             "workload": "512 graphs seeds 1000-1511, %d edges in total, exact (2,3) and (3,4)" % tot_m,
             "pairs": res, "one_by_one_ms": tot_one, "batched_ms": tot_b, "speedup": tot_one / tot_b,
-            "batched_form": "disjoint union, its orientation and index (timed), then counts + one persistent peel "
-                            "launch + construct-tree replayed from a CUDA graph (timed; capturing it is not)",
+            "batched_form": "nh_batch_prepare (disjoint union, its orientation and index; timed), then nh_batch_run "
+                            "(counts + one persistent peel launch + construct-tree) replayed from a CUDA graph "
+                            "(timed; capturing it is not)",
             "autotuned": {"max_group": tuned["best"][0], "task_items": tuned["best"][1],
                           "times_ms": {"%d,%d" % k: v for k, v in tuned["times_ms"].items()}}}
 

@@ -122,7 +122,8 @@ int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uin
  * uf is compressed in place.  Outputs: parent int32[n_r + n_nodes] (entries 0..n_r-1: node of
  * each r-clique or -1; entries n_r + j: parent node of node j or -1) -- the caller passes room
  * for 2*n_r entries; label uint32[n_r] (label[j] = level of node j); *n_nodes (host).
- * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_CUDA. */
+ * Errors: NH_ERR_INVALID (also: uf holds a cycle, so it is no union-find forest), NH_ERR_OOM,
+ * NH_ERR_CUDA. */
 int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                       int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
@@ -136,7 +137,7 @@ int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int3
  *    r-cliques (about 5.3 MB); every device that loads the library holds it until the process
  *    exits.  Larger n_r returns NH_ERR_INVALID before any device work.
  *  - The first call on a device looks up the array's device address (once per device, with that
- *    device current); make that first call before any stream capture that includes this call.
+ *    device current); make that first call before any stream capture begins on that device.
  *  - All calls share the one array: calls whose device work overlaps (on different streams, or
  *    from different host threads) race and corrupt each other's results -- serialise them.
  *  - The call synchronises `stream` before returning (it returns *n_nodes on the host). */
@@ -227,6 +228,28 @@ int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t* off_out, 
                    void* stream);
 /* rbase int64[n_graphs+1] (host): first r-clique id of each graph of a union built from vbase */
 int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream);
+
+/* a12 -- a batch as one library object.  nh_batch_prepare copies the graphs into their disjoint
+ * union (owned by the handle), builds its orientation and its r-clique index (r = 1, 2, 3), and
+ * returns *n_r (host) = the union's r-cliques; it synchronises `stream` (sizes come back to the
+ * host).  nh_batch_run then enqueues, for one s, exactly what nh_hierarchy_enqueue does on the
+ * union -- counts, the persistent peel with link-efficient (one launch for every graph of the
+ * batch) and construct-tree -- with no host synchronisation, so the caller can capture it into a
+ * CUDA graph and replay it; outputs and res as nh_hierarchy_enqueue (n_r-sized arrays of the
+ * union).  The r-cliques of graph g are [rbase[g], rbase[g+1]) (nh_batch_bases, host arrays of
+ * n_graphs + 1 entries; vbase likewise for vertices); core numbers and hierarchy nodes never mix
+ * graphs.  nh_batch_node_bases (after a run, synchronises `stream`) writes nbase (host,
+ * n_graphs + 1): the nodes of graph g are [nbase[g], nbase[g+1]), n_nodes = res[2].
+ * The paper has no counterpart (it runs one graph at a time).  The graphs' CSRs are only read
+ * by nh_batch_prepare.  Errors: NH_ERR_INVALID (bad descriptor, r outside 1..3, more than 2^31
+ * vertices in all), NH_ERR_UNSUPPORTED (pair), NH_ERR_OOM, NH_ERR_TABLE_FULL, NH_ERR_CUDA. */
+typedef struct nh_batch nh_batch;
+int nh_batch_prepare(const nh_graph_desc* graphs, int n_graphs, int r, nh_batch** out, int64_t* n_r, void* stream);
+int nh_batch_bases(const nh_batch* b, int64_t* vbase, int64_t* rbase);
+int nh_batch_run(nh_batch* b, int s, uint32_t* cnt, uint32_t* core, uint32_t* round, int32_t* uf, int32_t* L,
+                 int32_t* parent, uint32_t* label, int64_t* res, void* stream);
+int nh_batch_node_bases(const nh_batch* b, const int32_t* parent, int64_t n_nodes, int64_t* nbase, void* stream);
+void nh_batch_free(nh_batch* b);
 
 /* The whole exact path for one (r,s) on an existing r-clique index -- s-clique counts (as
  * nh_count_s_cliques), the peel with link-efficient in link mode 0 (as nh_peel_and_link) and

@@ -230,6 +230,11 @@ int nh_count_impl(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cn
 int nh_schedule_items(const nh_oriented* o, const float* vertex_cost, int32_t** order, unsigned long long** next,
                       cudaStream_t st);
 
+// tile of the device-wide scan (threads per block x items per thread); a scan of n entries uses
+// ceil(n / kNhScanTile) block sums
+constexpr int kNhScanThreads = 256;
+constexpr int kNhScanItems = 8;
+constexpr int kNhScanTile = kNhScanThreads * kNhScanItems;
 // exclusive prefix sum of 32-bit (or 64-bit) counts into int64 offsets, out[n] = total
 int nh_exclusive_scan_u32(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t st);
 int nh_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
@@ -240,8 +245,9 @@ int nh_exclusive_scan_u32_into(const uint32_t* in, int64_t* out, int64_t n, int6
 // stream-ordered pieces of the path (no host synchronisation; results stay in device words)
 int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, const float* vertex_cost,
                      float* measure, unsigned long long* dcount, int* status, cudaStream_t st);
+// status_dev (int64, may be null): set to NH_ERR_INVALID when a union-find walk finds a cycle
 int nh_tree_enqueue(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
-                    uint32_t* label, int64_t* n_nodes_dev, cudaStream_t st);
+                    uint32_t* label, int64_t* n_nodes_dev, int64_t* status_dev, cudaStream_t st);
 
 // allocation helpers (stream ordered)
 template <typename T>

@@ -341,7 +341,7 @@ extern "C" int nh_hierarchy_enqueue(const nh_oriented* o, const nh_rindex* ri, i
   }
   nh_free(cstat, st);
   if (!rc) rc = run_peel(true, o, ri, s, cnt, core, round, uf, L, 0, 0.0, nullptr, res, st);
-  if (!rc) rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, res + 2, st);
+  if (!rc) rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, res + 2, res, st);
   return rc;
 }
 

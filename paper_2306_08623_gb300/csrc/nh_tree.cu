@@ -7,14 +7,22 @@
 
 namespace {
 
-// full path compression: uf[i] = root of i (parents only ever point to ancestors)
-__global__ void k_tree_roots(int64_t n_r, int32_t* __restrict__ uf, uint32_t* __restrict__ own) {
+// full path compression: uf[i] = root of i (parents only ever point to ancestors).  A path in a
+// forest of n_r entries has fewer than n_r steps; a walk that takes n_r steps has met a cycle (a
+// corrupt uf), records NH_ERR_INVALID in *status (first error wins) and leaves uf[i] as it was.
+__global__ void k_tree_roots(int64_t n_r, int32_t* __restrict__ uf, uint32_t* __restrict__ own,
+                             int64_t* __restrict__ status) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t x = (int32_t)i;
-    for (int it = 0; it < (1 << 24); ++it) {
+    int64_t it = 0;
+    for (; it < n_r; ++it) {
       const int32_t p = __ldcg(uf + x);
       if (p == x) break;
       x = p;
+    }
+    if (it == n_r) {
+      atomicCAS(reinterpret_cast<unsigned long long*>(status), 0ull, (unsigned long long)(int64_t)NH_ERR_INVALID);
+      continue;
     }
     __stcg(uf + i, x);
     atomicAdd(own + x, 1u);
@@ -55,7 +63,7 @@ __global__ void k_tree_write(int64_t n_r, const int32_t* __restrict__ uf, const 
 // Stream-ordered construct-tree: launches only; the node count lands in the device word
 // n_nodes_dev.  n_r >= 1, arguments checked by the caller.
 int nh_tree_enqueue(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L, int32_t* parent,
-                    uint32_t* label, int64_t* n_nodes_dev, cudaStream_t st) {
+                    uint32_t* label, int64_t* n_nodes_dev, int64_t* status_dev, cudaStream_t st) {
   uint32_t *own = nullptr, *nch = nullptr, *flag = nullptr;
   int64_t* nid = nullptr;
   int rc = NH_OK;
@@ -67,7 +75,7 @@ int nh_tree_enqueue(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_
   const unsigned blocks = nh_blocks_for(n_r, 256, 152 * 32);
   cudaMemsetAsync(own, 0, sizeof(uint32_t) * n_r, st);
   cudaMemsetAsync(nch, 0, sizeof(uint32_t) * n_r, st);
-  k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own);
+  k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own, status_dev);
   nh_note_launch();
   k_tree_children<<<blocks, 256, 0, st>>>(n_r, uf, L, nch);
   nh_note_launch();
@@ -92,15 +100,17 @@ extern "C" int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf,
     return NH_OK;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  int64_t* nn_dev = nullptr;
-  int rc = nh_alloc(&nn_dev, 1, st);
+  int64_t* nn_dev = nullptr;  // {n_nodes, status}
+  int rc = nh_alloc(&nn_dev, 2, st);
   if (rc) return rc;
-  rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, nn_dev, st);
-  int64_t nn = 0;
-  if (!rc) cudaMemcpyAsync(&nn, nn_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  cudaMemsetAsync(nn_dev, 0, 2 * sizeof(int64_t), st);
+  rc = nh_tree_enqueue(n_r, core, uf, L, parent, label, nn_dev, nn_dev + 1, st);
+  int64_t nn[2] = {0, 0};
+  if (!rc) cudaMemcpyAsync(nn, nn_dev, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   nh_free(nn_dev, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
-  if (!rc && n_nodes) *n_nodes = nn;
+  if (!rc && nn[1]) rc = (int)nn[1];
+  if (!rc && n_nodes) *n_nodes = nn[0];
   return rc;
 }
 
@@ -124,8 +134,10 @@ constexpr size_t kOwnOff = 0;
 constexpr size_t kNchOff = kOwnOff + align_up(sizeof(uint32_t) * kNoAllocMax);
 constexpr size_t kFlagOff = kNchOff + align_up(sizeof(uint32_t) * kNoAllocMax);
 constexpr size_t kNidOff = kFlagOff + align_up(sizeof(uint32_t) * kNoAllocMax);
+constexpr int64_t kBsumSlots = (kNoAllocMax + kNhScanTile - 1) / kNhScanTile;  // scan block sums
 constexpr size_t kBsumOff = kNidOff + align_up(sizeof(int64_t) * (kNoAllocMax + 1));
-constexpr size_t kScratchBytes = kBsumOff + align_up(sizeof(int64_t) * (kNoAllocMax / 2048 + 2));
+constexpr size_t kStatusOff = kBsumOff + align_up(sizeof(int64_t) * kBsumSlots);
+constexpr size_t kScratchBytes = kStatusOff + align_up(sizeof(int64_t));
 
 }  // namespace
 
@@ -174,24 +186,30 @@ extern "C" int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int3
   uint32_t* flag = reinterpret_cast<uint32_t*>(base + kFlagOff);
   int64_t* nid = reinterpret_cast<int64_t*>(base + kNidOff);
   int64_t* bsum = reinterpret_cast<int64_t*>(base + kBsumOff);
-  // the array keeps the previous call's contents: the counters must start at zero
+  int64_t* status = reinterpret_cast<int64_t*>(base + kStatusOff);
+  if (nh_scan_u32_blocks(n_r) > kBsumSlots) return NH_ERR_INTERNAL;
+  // the array keeps the previous call's contents: the counters and the status must start at zero
   if (cudaMemsetAsync(own, 0, sizeof(uint32_t) * n_r, st) != cudaSuccess ||
-      cudaMemsetAsync(nch, 0, sizeof(uint32_t) * n_r, st) != cudaSuccess)
+      cudaMemsetAsync(nch, 0, sizeof(uint32_t) * n_r, st) != cudaSuccess ||
+      cudaMemsetAsync(status, 0, sizeof(int64_t), st) != cudaSuccess)
     return NH_ERR_CUDA;
   const unsigned blocks = nh_blocks_for(n_r, 256, 152 * 32);
-  k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own);
+  k_tree_roots<<<blocks, 256, 0, st>>>(n_r, uf, own, status);
   k_tree_children<<<blocks, 256, 0, st>>>(n_r, uf, L, nch);
   k_tree_flags<<<blocks, 256, 0, st>>>(n_r, uf, own, nch, flag);
   nh_note_launch(3);
   rc = nh_exclusive_scan_u32_into(flag, nid, n_r, bsum, st);
-  int64_t nn = 0;
+  int64_t nn = 0, bad = 0;
   if (!rc) {
     k_tree_write<<<blocks, 256, 0, st>>>(n_r, uf, L, core, flag, nid, parent, label);
     nh_note_launch();
-    if (cudaMemcpyAsync(&nn, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = NH_ERR_CUDA;
+    if (cudaMemcpyAsync(&nn, nid + n_r, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&bad, status, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = NH_ERR_CUDA;
   }
   if (cudaGetLastError() != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+  if (!rc && bad) rc = (int)bad;
   if (!rc && n_nodes) *n_nodes = nn;
   return rc;
 }

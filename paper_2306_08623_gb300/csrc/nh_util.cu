@@ -3,9 +3,9 @@
 
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanThreads = kNhScanThreads;
+constexpr int kScanItems = kNhScanItems;
+constexpr int kScanTile = kNhScanTile;
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
   const int lane = threadIdx.x & 31;

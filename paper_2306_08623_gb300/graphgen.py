@@ -184,14 +184,19 @@ def shared_hubs(commons, inner_deg: float, seed: int, extra: int = 0):
     return csr_from_pairs(n, np.concatenate(us), np.concatenate(vs))
 
 
+def batch_member_shape(seed: int):
+    """(n, mean degree, family) of one graph of the 512-graph batch, without building it."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
+    md = float(rng.uniform(8.0, 40.0))
+    return n, md, seed % 3
+
+
 def batch_member(seed: int):
     """One graph of the 512-graph batch: n log-uniform in [1e3, 2e5], mean degree U[8, 40],
     family by seed mod 3: Erdos-Renyi, R-MAT (scale ceil(log2 n), ids >= n dropped), Chung-Lu
     with max(1, n/2000) planted cliques."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
-    md = float(rng.uniform(8.0, 40.0))
-    fam = seed % 3
+    n, md, fam = batch_member_shape(seed)
     if fam == 0:
         return erdos_renyi(n, int(n * md / 2), seed)
     if fam == 1:

@@ -77,6 +77,11 @@ def lib():
             "nh_vertex_features": (I32, [P, P, P]),
             "nh_batch_union": (I32, [P, I32, P, P, P, P]),
             "nh_rindex_bases": (I32, [P, P, I32, P, P]),
+            "nh_batch_prepare": (I32, [P, I32, I32, ctypes.POINTER(P), ctypes.POINTER(I64), P]),
+            "nh_batch_bases": (I32, [P, P, P]),
+            "nh_batch_run": (I32, [P, I32, P, P, P, P, P, P, P, P, P]),
+            "nh_batch_node_bases": (I32, [P, P, I64, P, P]),
+            "nh_batch_free": (None, [P]),
             "nh_listing_cost": (I32, [P, P, I32, P, P]),
             "nh_degree_cost": (I32, [P, I32, P, P]),
             "nh_mlp_train": (I32, [P, P, I64, I64, I32, ctypes.c_float, ctypes.c_uint64, P,
@@ -385,6 +390,56 @@ def rindex_bases(ri: RIndex, vbase, stream=None):
     _check("nh_rindex_bases", lib().nh_rindex_bases(ri.handle, vbase.ctypes.data_as(P), len(vbase) - 1,
                                                     out.ctypes.data_as(P), _stream(stream)))
     return out
+
+
+class Batch:
+    """A batch of graphs prepared as one disjoint union (nh_batch_prepare): its orientation and
+    r-clique index live in the handle; run(s, buf) enqueues counts, the persistent peel and
+    construct-tree over every graph at once (capturable).  vbase / rbase: the first vertex /
+    r-clique of every graph in the union (n_graphs + 1 entries)."""
+
+    def __init__(self, graphs, r: int, stream=None):
+        import numpy as np
+        descs = (GraphDesc * len(graphs))()
+        for i, (off, adj) in enumerate(graphs):
+            descs[i] = GraphDesc(off.numel() - 1, adj.numel(), off.data_ptr(), adj.data_ptr() if adj.numel() else None)
+        h, n_r = P(), I64()
+        _check("nh_batch_prepare", lib().nh_batch_prepare(descs, len(graphs), r, ctypes.byref(h), ctypes.byref(n_r),
+                                                          _stream(stream)))
+        self.handle, self.r, self.n_r, self.n_graphs = h, r, n_r.value, len(graphs)
+        self.vbase = np.zeros(len(graphs) + 1, dtype=np.int64)
+        self.rbase = np.zeros(len(graphs) + 1, dtype=np.int64)
+        _check("nh_batch_bases", lib().nh_batch_bases(h, self.vbase.ctypes.data_as(P), self.rbase.ctypes.data_as(P)))
+
+    def buffers(self) -> dict:
+        return hierarchy_buffers(self)
+
+    def run(self, s: int, buf: dict, stream=None):
+        _check("nh_batch_run", lib().nh_batch_run(
+            self.handle, s, _dptr(buf["cnt"]), _dptr(buf["core"]), _dptr(buf["round"]), _dptr(buf["uf"]),
+            _dptr(buf["L"]), _dptr(buf["parent"]), _dptr(buf["label"]), _dptr(buf["res"]), _stream(stream)))
+
+    def capture(self, s: int, buf: dict):
+        """run(s, buf) captured into a CUDA graph after one eager call; replay() reruns it."""
+        self.run(s, buf)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+            self.run(s, buf)
+        return g
+
+    def node_bases(self, parent: torch.Tensor, n_nodes: int, stream=None):
+        import numpy as np
+        out = np.zeros(self.n_graphs + 1, dtype=np.int64)
+        _check("nh_batch_node_bases", lib().nh_batch_node_bases(self.handle, _dptr(parent), int(n_nodes),
+                                                                out.ctypes.data_as(P), _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nh_batch_free(self.handle)
+            self.handle = None
 
 
 def set_peel_max_group(g: int):

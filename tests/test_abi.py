@@ -23,7 +23,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for want in ["nh_build_orientation", "nh_index_r_cliques", "nh_count_s_cliques", "nh_peel_and_link",
-                 "nh_construct_tree", "nh_approx_nucleus", "nh_oriented_free", "nh_rindex_free"]:
+                 "nh_construct_tree", "nh_approx_nucleus", "nh_oriented_free", "nh_rindex_free", "nh_batch_run"]:
         assert want in names
 
 

@@ -203,6 +203,21 @@ def test_construct_tree_worked_trace(nc):
     assert got == want
 
 
+def test_construct_tree_rejects_cyclic_uf(nc):
+    """A uf array with a cycle is no union-find forest: construct-tree reports NH_ERR_INVALID (its
+    root walks are bounded by n_r steps) and a valid call afterwards still succeeds."""
+    n = 5
+    core = torch.ones(n, dtype=torch.int32, device="cuda")
+    uf = torch.tensor([1, 2, 0, 3, 3], dtype=torch.int32, device="cuda")  # 0 -> 1 -> 2 -> 0
+    L = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(nc.NucleusError) as ei:
+        nc.construct_tree(core, uf, L)
+    assert ei.value.status == 1  # NH_ERR_INVALID
+    uf = torch.tensor([0, 0, 0, 3, 3], dtype=torch.int32, device="cuda")
+    parent, label, nn = nc.construct_tree(core, uf, L)
+    assert nn == 2 and sorted(u32(label).tolist()) == [1, 1]
+
+
 def test_link_pairs_concurrent_matches_definition(nc):
     """All link calls of the definitional reading (each s-clique: its min-core member with every
     other member), shuffled and issued at once, then construct-tree: equals the oracle."""
