@@ -145,6 +145,18 @@ int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int3
 int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                               int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
+/* c-(r,s) nuclei from a hierarchy (§8's use of the hierarchy for dense subgraphs; §3: the
+ * c-(r,s) nuclei are the connected components of the r-cliques of core >= c).  Removing every node
+ * of level < c from the tree of nh_construct_tree / nh_hierarchy_two_phase leaves a forest whose
+ * trees are exactly the c-nuclei.  Inputs (device): parent int32[n_r + n_nodes] and label
+ * uint32[n_nodes] in that layout.  Output (device, caller-owned): nucleus int32[n_r] = the node id
+ * of the top of the c-nucleus holding r-clique i, or -1 when i's core is below c (or i is in no
+ * node).  *n_nuclei (host, may be NULL; when given the call synchronises `stream`) = the number of
+ * c-nuclei.  Entries out of range in parent are treated as absent.
+ * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_CUDA. */
+int nh_cut_hierarchy(int64_t n_r, int64_t n_nodes, const int32_t* parent, const uint32_t* label, uint32_t c,
+                     int32_t* nucleus, int64_t* n_nuclei, void* stream);
+
 /* §7.4 practical two-phase hierarchy (anh-te), from final core numbers: levels c = kmax .. 1 are
  * processed with one union-find; at level c every r-clique of core c re-lists its s-cliques and
  * joins the members of those whose least member core is c (the definition of §3); each component

@@ -213,3 +213,83 @@ extern "C" int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int3
   if (!rc && n_nodes) *n_nodes = nn;
   return rc;
 }
+
+// ---------------------------------------------------------------------------------------------
+// nh_cut_hierarchy: the c-(r,s) nuclei read off a hierarchy (§8, dense subgraphs).  Removing every
+// node of level < c leaves a forest whose trees are the c-nuclei; each r-clique maps to the top
+// node of the tree that holds its smallest node.  Node-level pointer jumping: up[N] starts at N's
+// parent when that parent keeps level >= c (else N itself), and up[N] = up[up[N]] is repeated
+// ceil(log2 n_nodes) + 1 times, which reaches the top of any path of at most n_nodes nodes.
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+__global__ void k_cut_init(int64_t n_r, int64_t n_nodes, const int32_t* __restrict__ parent,
+                           const uint32_t* __restrict__ label, uint32_t c, int32_t* __restrict__ up,
+                           unsigned long long* __restrict__ n_top) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = parent[n_r + j];
+    const bool keep_up = p >= 0 && p < n_nodes && label[p] >= c;
+    up[j] = keep_up ? p : (int32_t)j;
+    if (!keep_up && label[j] >= c) atomicAdd(n_top, 1ull);
+  }
+}
+
+__global__ void k_cut_jump(int64_t n_nodes, const int32_t* __restrict__ up_in, int32_t* __restrict__ up_out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += (int64_t)gridDim.x * blockDim.x)
+    up_out[j] = up_in[up_in[j]];
+}
+
+__global__ void k_cut_leaves(int64_t n_r, int64_t n_nodes, const int32_t* __restrict__ parent,
+                             const uint32_t* __restrict__ label, uint32_t c, const int32_t* __restrict__ up,
+                             int32_t* __restrict__ nucleus) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_r; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t N = parent[i];
+    nucleus[i] = (N >= 0 && N < n_nodes && label[N] >= c) ? up[N] : -1;
+  }
+}
+
+}  // namespace
+
+extern "C" int nh_cut_hierarchy(int64_t n_r, int64_t n_nodes, const int32_t* parent, const uint32_t* label,
+                                uint32_t c, int32_t* nucleus, int64_t* n_nuclei, void* stream) {
+  if (n_r < 0 || n_nodes < 0 || n_nodes > n_r || n_r >= (1ll << 31) || (n_r > 0 && (!parent || !nucleus)) ||
+      (n_nodes > 0 && !label))
+    return NH_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_r == 0) {
+    if (n_nuclei) *n_nuclei = 0;
+    return NH_OK;
+  }
+  int32_t *up0 = nullptr, *up1 = nullptr;
+  unsigned long long* cnt = nullptr;
+  int rc = NH_OK;
+  if ((rc = nh_alloc(&up0, n_nodes, st)) || (rc = nh_alloc(&up1, n_nodes, st)) || (rc = nh_alloc(&cnt, 1, st))) {
+    nh_free(up0, st); nh_free(up1, st); nh_free(cnt, st);
+    return rc;
+  }
+  cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+  const unsigned bn = nh_blocks_for(n_nodes, 256, 152 * 16), br = nh_blocks_for(n_r, 256, 152 * 16);
+  if (n_nodes > 0) {
+    k_cut_init<<<bn, 256, 0, st>>>(n_r, n_nodes, parent, label, c, up0, cnt);
+    nh_note_launch();
+    int rounds = 1;
+    while ((1ll << (rounds - 1)) < n_nodes) rounds++;
+    for (int k = 0; k < rounds; k++) {
+      k_cut_jump<<<bn, 256, 0, st>>>(n_nodes, up0, up1);
+      nh_note_launch();
+      int32_t* t = up0; up0 = up1; up1 = t;
+    }
+  }
+  k_cut_leaves<<<br, 256, 0, st>>>(n_r, n_nodes, parent, label, c, up0, nucleus);
+  nh_note_launch();
+  unsigned long long h = 0;
+  if (n_nuclei) cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (cudaGetLastError() != cudaSuccess) rc = NH_ERR_CUDA;
+  nh_free(up0, st); nh_free(up1, st); nh_free(cnt, st);
+  if (n_nuclei) {
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
+    if (!rc) *n_nuclei = (int64_t)h;
+  }
+  return rc;
+}

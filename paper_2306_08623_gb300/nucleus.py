@@ -82,6 +82,7 @@ def lib():
             "nh_batch_run": (I32, [P, I32, P, P, P, P, P, P, P, P, P]),
             "nh_batch_node_bases": (I32, [P, P, I64, P, P]),
             "nh_batch_free": (None, [P]),
+            "nh_cut_hierarchy": (I32, [I64, I64, P, P, ctypes.c_uint32, P, ctypes.POINTER(I64), P]),
             "nh_listing_cost": (I32, [P, P, I32, P, P]),
             "nh_degree_cost": (I32, [P, I32, P, P]),
             "nh_mlp_train": (I32, [P, P, I64, I64, I32, ctypes.c_float, ctypes.c_uint64, P,
@@ -273,6 +274,16 @@ def capture_hierarchy(o: Oriented, ri: RIndex, s: int, buf: dict):
     with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
         hierarchy_enqueue(o, ri, s, buf)
     return g
+
+
+def cut_hierarchy(parent: torch.Tensor, label: torch.Tensor, n_r: int, n_nodes: int, c: int, stream=None):
+    """c-(r,s) nuclei from a hierarchy: per r-clique the node id of the top of its c-nucleus (-1
+    when its core is below c), and the number of c-nuclei."""
+    out = torch.empty(max(n_r, 1), dtype=torch.int32, device="cuda")
+    nn = I64()
+    _check("nh_cut_hierarchy", lib().nh_cut_hierarchy(n_r, n_nodes, _dptr(parent), _dptr(label), int(c), _dptr(out),
+                                                      ctypes.byref(nn), _stream(stream)))
+    return out[:n_r], nn.value
 
 
 def construct_tree_noalloc(core: torch.Tensor, uf: torch.Tensor, L: torch.Tensor, parent: torch.Tensor,
