@@ -19,8 +19,10 @@
  *    before returning.  No entry point aborts, traps or prints.
  *  - r-clique ids: the canonical order is lexicographic by the sorted vertex tuple, so id i of
  *    (r=1) is vertex i, of (r=2) the i-th edge (u<v) in lexicographic order, of (r=3) the i-th
- *    triangle (a<b<c) in lexicographic order.
- *  - Supported (r,s): (1,2), (1,3), (2,3), (2,4), (3,4).  Others return NH_ERR_UNSUPPORTED.
+ *    triangle (a<b<c) in lexicographic order, and so on for r up to 6.
+ *  - Supported (r,s): every 1 <= r < s <= 7.  (1,2), (1,3), (2,3), (2,4), (3,4) run specialised
+ *    kernels (persistent peel, no host round trip per round); the other pairs run the generic
+ *    path (see "Pairs" below).  Others return NH_ERR_UNSUPPORTED.
  *  - Counts and core numbers are uint32.  Counting checks every increment and returns
  *    NH_ERR_COUNT_OVERFLOW when an s-clique-degree would exceed 2^32 - 1 (core numbers and
  *    approximate values never exceed the s-clique-degree).
@@ -80,13 +82,22 @@ void nh_oriented_free(nh_oriented* o);
 
 /* a2 -- index the r-cliques (the keys of table U in Alg. 3).  r = 1: vertices; r = 2: edges;
  * r = 3: triangles, enumerated per lexicographic edge (a,b) as the common neighbours c > b, and
- * inserted into a device open-addressing hash table keyed by (edge id of (a,b), c).
+ * inserted into a device open-addressing hash table keyed by (edge id of (a,b), c); r = 4..6: the
+ * same one level up -- per (r-1)-clique P in lexicographic order, the common neighbours c above
+ * P's largest vertex, keyed by (id of P, c) -- a chain of tables ending at the triangles.  Ids
+ * are lexicographic in every case.
  * *n_r (host) receives the number of r-cliques.
  * Errors: NH_ERR_INVALID, NH_ERR_OOM, NH_ERR_TABLE_FULL, NH_ERR_CUDA. */
 int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, int64_t* n_r, void* stream);
 /* write the vertex tuples of all r-cliques, tuples[i*r + j] (int32, device, n_r*r entries) */
 int nh_rindex_tuples(const nh_rindex* ri, int32_t* tuples, void* stream);
 void nh_rindex_free(nh_rindex* ri);
+
+/* Pairs.  Every entry point that takes (r,s) accepts 1 <= r < s <= 7 (§1: r < s <= 7).  (1,2),
+ * (1,3), (2,3), (2,4) and (3,4) run the specialised kernels described below; every other pair runs
+ * the generic path: counting by recursive listing, the peel (exact or approximate) with one host
+ * round trip per round, and the hierarchy by link-efficient (Alg. 5) over every s-clique after the
+ * peel followed by construct-tree.  nh_hierarchy_enqueue takes the specialised pairs only. */
 
 /* a3 -- rec-list-cliques (Alg. 3, count step): cnt[R] = number of s-cliques containing R
  * (s-clique-degree, §3), for every r-clique R, found by recursive intersection of out-lists of
@@ -144,6 +155,19 @@ int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int3
 #define NH_TREE_NOALLOC_MAX (1 << 18)
 int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                               int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
+
+/* NEXT-3 / §7.2 -- link-basic and construct-tree-basic (Alg. 4), the ablation the paper measures
+ * against link-efficient: one union-find per level 1..kmax (kmax * n_r int32 of device memory:
+ * NH_ERR_OOM when that exceeds 80 % of the free memory); every s-clique unites its member of least
+ * core with each other member in every level up to c_S (the definitional reading of §3, the same
+ * connections the interleaved peel makes); then, from level kmax down to 1, every component of at
+ * least two r-cliques that is not already, as a set, a component one level up becomes a node of
+ * that level adopting its members' current top nodes.  Inputs: the core numbers of the exact peel.
+ * Outputs as nh_construct_tree (parent int32[2 n_r], label uint32[n_r], *n_nodes host); *unites
+ * (host, may be NULL) = successful unions over all levels.  Synchronises `stream`.
+ * Errors: NH_ERR_INVALID, NH_ERR_UNSUPPORTED, NH_ERR_OOM, NH_ERR_INTERNAL, NH_ERR_TIMEOUT, NH_ERR_CUDA. */
+int nh_hierarchy_basic(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* core, int32_t* parent,
+                       uint32_t* label, int64_t* n_nodes, uint64_t* unites, void* stream);
 
 /* c-(r,s) nuclei from a hierarchy (§8's use of the hierarchy for dense subgraphs; §3: the
  * c-(r,s) nuclei are the connected components of the r-cliques of core >= c).  Removing every node

@@ -75,6 +75,7 @@ extern "C" int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t
 
 extern "C" int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream) {
   if (!ri || !vbase || !rbase || n_graphs < 1) return NH_ERR_INVALID;
+  if (ri->r > 3) return NH_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   if (ri->r == 1) {
     for (int g = 0; g <= n_graphs; g++) rbase[g] = vbase[g];

@@ -248,7 +248,8 @@ int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t*
                      float* measure, unsigned long long* dcount, int* status, cudaStream_t st) {
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
-  if (!nh_supported(r, s) && !(r == 1 && s == 4)) return NH_ERR_UNSUPPORTED;
+  const bool special = nh_supported(r, s) || (r == 1 && s == 4);
+  if (!special && !nh_generic_pair(r, s)) return NH_ERR_UNSUPPORTED;
   if (!cnt && ri->n_r > 0) return NH_ERR_INVALID;
   GView g = make_view(o, ri);
   if (r == 1 && s == 2) {
@@ -269,7 +270,9 @@ int nh_count_enqueue(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t*
     k_fill_u32<<<nh_blocks_for(ri->n_r, 256, 152 * 32), 256, 0, st>>>(ri->n_r, cnt, (uint32_t)g_nh_inject_count_base);
     nh_note_launch();
   }
-  if (s == 3) {
+  if (!special) {
+    rc = nh_count_generic(o, ri, s, cnt, dcount, status, st);  // every other pair: recursive listing
+  } else if (s == 3) {
     const void* fn = (r == 1) ? (const void*)k_count_s3<1> : (const void*)k_count_s3<2>;
     int grid = grid_for(fn, kThreads, 0);
     if (vertex_cost && (rc = nh_schedule_items(o, vertex_cost, &order, &next, st))) return rc;

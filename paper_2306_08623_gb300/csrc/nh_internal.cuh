@@ -72,6 +72,7 @@ struct nh_rindex {
   int32_t* t2ea;
   int32_t* t2eb;
   uint32_t* t2cost;
+  nh_rindex* prev;  // r >= 4: the index of the (r-1)-cliques this one extends (owned)
   cudaStream_t stream;
 };
 
@@ -277,3 +278,14 @@ static inline int nh_binom(int n, int k) {
 static inline bool nh_supported(int r, int s) {
   return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
 }
+// pairs served by the generic path (nh_generic.cu): every other 1 <= r < s <= 7
+static inline bool nh_generic_pair(int r, int s) { return r >= 1 && s > r && s <= 7 && !nh_supported(r, s); }
+// generic path entry points (nh_generic.cu)
+int nh_index_generic(const nh_oriented* o, nh_rindex* prev, int r, nh_rindex* out, cudaStream_t st);
+int nh_count_generic(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt, unsigned long long* dcount,
+                     int* status, cudaStream_t st);
+int nh_peel_generic(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* cnt, uint32_t* val,
+                    uint32_t* round, int32_t* uf, int32_t* L, int link_mode, double delta, nh_peel_stats* stats,
+                    cudaStream_t st);
+int nh_label_hierarchy_generic(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* labels,
+                               int32_t* parent, uint32_t* label, int64_t* n_nodes, cudaStream_t st);

@@ -368,6 +368,7 @@ void free_rindex(nh_rindex* ri) {
   cudaFree(ri->tri); cudaFree(ri->tedge); cudaFree(ri->toff); cudaFree(ri->table);
   cudaFree(ri->etoff); cudaFree(ri->etw); cudaFree(ri->ettid);
   cudaFree(ri->t2off); cudaFree(ri->t2w); cudaFree(ri->t2ea); cudaFree(ri->t2eb); cudaFree(ri->t2cost);
+  if (ri->prev) free_rindex(ri->prev);
   delete ri;
 }
 
@@ -489,9 +490,26 @@ extern "C" int nh_oriented_info(const nh_oriented* o, int64_t* n, int64_t* m, in
 extern "C" void nh_oriented_free(nh_oriented* o) { free_oriented(o); }
 
 extern "C" int nh_index_r_cliques(const nh_oriented* o, int r, nh_rindex** out, int64_t* n_r, void* stream) {
-  if (!out || !o || r < 1 || r > 3) return NH_ERR_INVALID;
+  if (!out || !o || r < 1 || r > 6) return NH_ERR_INVALID;
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
+  if (r >= 4) {
+    // r = 4..6: a chain of tables, each r-clique keyed by the id of its first r-1 vertices
+    nh_rindex* prev = nullptr;
+    int rc = nh_index_r_cliques(o, r - 1, &prev, nullptr, stream);
+    if (rc) return rc;
+    nh_rindex* ri = new nh_rindex();
+    ri->r = r; ri->o = o; ri->stream = st; ri->prev = prev;
+    rc = nh_index_generic(o, prev, r, ri, st);
+    if (rc) {
+      cudaStreamSynchronize(st);
+      free_rindex(ri);
+      return rc;
+    }
+    if (n_r) *n_r = ri->n_r;
+    *out = ri;
+    return NH_OK;
+  }
   nh_rindex* ri = new nh_rindex();
   ri->r = r; ri->o = o; ri->stream = st;
   if (r == 1) ri->n_r = o->n;
@@ -616,6 +634,9 @@ extern "C" int nh_rindex_tuples(const nh_rindex* ri, int32_t* tuples, void* stre
   if (!ri || (!tuples && ri->n_r > 0)) return NH_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   if (ri->n_r == 0) return NH_OK;
+  if (ri->r >= 4)
+    return cudaMemcpyAsync(tuples, ri->tri, sizeof(int32_t) * (size_t)ri->r * (size_t)ri->n_r, cudaMemcpyDeviceToDevice,
+                           st) == cudaSuccess ? NH_OK : NH_ERR_CUDA;
   k_tuples<<<nh_blocks_for(ri->n_r, 256, 152 * 32), 256, 0, st>>>(ri->r, ri->n_r, ri->o->eu, ri->o->ev, ri->tri, tuples);
   nh_note_launch();
   return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;

@@ -124,6 +124,14 @@ __global__ void k_link_drain(LinkEnv E) {
   }
 }
 
+// one drain step of link-efficient's overflow queue: swap the queues, re-run the deferred calls
+int link_drain_round(const LinkEnv& E, cudaStream_t st) {
+  k_link_swap<<<1, 1, 0, st>>>(E.ctl, E.ovf_cap);
+  k_link_drain<<<152 * 8, 128, 0, st>>>(E);
+  nh_note_launch(2);
+  return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ERR_CUDA;
+}
+
 int peel_launch_pair(int r, int s, bool exact, PeelArgs& A, cudaStream_t st) {
   if (r == 1 && s == 2) return peel_launch_12(exact, A, st);
   if (r == 1 && s == 3) return peel_launch_13(exact, A, st);
@@ -161,6 +169,15 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   if (res_dev && !exact) return NH_ERR_INVALID;
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
+  if (nh_generic_pair(r, s)) {
+    // other pairs: Alg. 3 / Alg. 2 rounds with one host round trip each (not stream-ordered)
+    if (res_dev) return NH_ERR_UNSUPPORTED;
+    if (ri->n_r > 0 && (!cnt || !val || !round)) return NH_ERR_INVALID;
+    if (exact && (link_mode < 0 || link_mode > 2 || (link_mode < 2 && ri->n_r > 0 && (!uf || !L))))
+      return NH_ERR_INVALID;
+    if (!exact && !(delta > 0.0)) return NH_ERR_INVALID;
+    return nh_peel_generic(exact, o, ri, s, cnt, val, round, uf, L, exact ? link_mode : -1, delta, stats, st);
+  }
   if (stats) *stats = nh_peel_stats{};
   if (ri->n_r == 0 && nh_supported(r, s)) return NH_OK;  // arrays may be empty (null)
   if (!cnt || !val || !round) return NH_ERR_INVALID;
@@ -422,7 +439,7 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
                           uint32_t* label, int64_t* n_nodes, bool label_mode, void* stream) {
   if (!o || !ri || ri->o != o) return NH_ERR_INVALID;
   const int r = ri->r;
-  if (!nh_supported(r, s)) return NH_ERR_UNSUPPORTED;
+  if (!nh_supported(r, s) && !nh_generic_pair(r, s)) return NH_ERR_UNSUPPORTED;
   const int64_t n_r = ri->n_r;
   if (n_r == 0) {
     if (n_nodes) *n_nodes = 0;
@@ -430,6 +447,14 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   }
   if (!core || !parent || !label) return NH_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!nh_supported(r, s)) {
+    // other pairs: link-efficient over every s-clique at the level of its least member value,
+    // then construct-tree (the definitional hierarchy of those values; core numbers included)
+    int64_t nn = 0;
+    const int rc = nh_label_hierarchy_generic(o, ri, s, core, parent, label, &nn, st);
+    if (!rc && n_nodes) *n_nodes = nn;
+    return rc;
+  }
   PeelArgs A{};
   TreeOut T{};
   A.g = make_view(o, ri);

@@ -358,6 +358,9 @@ static __device__ void link_run(const LinkEnv& E, int32_t R0, int32_t Q0, LocalS
   }
 }
 
+// host: one drain step of the overflow queue of deferred link calls (nh_peel.cu)
+int link_drain_round(const LinkEnv& E, cudaStream_t st);
+
 // one out-of-line copy for the rarely taken call sites (keeps the kernels' code size down)
 // link-efficient counters of a link_run done out of line
 struct LinkDelta {

@@ -14,7 +14,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnucleus.so")
 
-SUPPORTED = ((1, 2), (1, 3), (2, 3), (2, 4), (3, 4))
+SPECIALISED = ((1, 2), (1, 3), (2, 3), (2, 4), (3, 4))  # persistent-peel pairs
+SUPPORTED = tuple((r, s) for s in range(2, 8) for r in range(1, s))  # every r < s <= 7
 LINK_MODES = {"def": 0, "pair": 1, "none": 2}
 
 
@@ -83,6 +84,7 @@ def lib():
             "nh_batch_node_bases": (I32, [P, P, I64, P, P]),
             "nh_batch_free": (None, [P]),
             "nh_cut_hierarchy": (I32, [I64, I64, P, P, ctypes.c_uint32, P, ctypes.POINTER(I64), P]),
+            "nh_hierarchy_basic": (I32, [P, P, I32, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_uint64), P]),
             "nh_listing_cost": (I32, [P, P, I32, P, P]),
             "nh_degree_cost": (I32, [P, I32, P, P]),
             "nh_mlp_train": (I32, [P, P, I64, I64, I32, ctypes.c_float, ctypes.c_uint64, P,
@@ -229,6 +231,20 @@ def hierarchy_two_phase(o: Oriented, ri: RIndex, s: int, core: torch.Tensor, str
     _check("nh_hierarchy_two_phase", lib().nh_hierarchy_two_phase(o.handle, ri.handle, s, _dptr(core), _dptr(parent),
                                                                   _dptr(label), ctypes.byref(nn), _stream(stream)))
     return parent[: n_r + nn.value], label[: nn.value], nn.value
+
+
+def hierarchy_basic(o: Oriented, ri: RIndex, s: int, core: torch.Tensor, stream=None):
+    """link-basic + construct-tree-basic (Alg. 4) from final core numbers; returns (parent, label,
+    n_nodes, unites) with parent / label like construct_tree."""
+    n_r = ri.n_r
+    parent = torch.empty(max(2 * n_r, 1), dtype=torch.int32, device="cuda")
+    label = torch.empty(max(n_r, 1), dtype=torch.int32, device="cuda")
+    nn = I64()
+    un = ctypes.c_uint64()
+    _check("nh_hierarchy_basic", lib().nh_hierarchy_basic(o.handle, ri.handle, s, _dptr(core), _dptr(parent),
+                                                          _dptr(label), ctypes.byref(nn), ctypes.byref(un),
+                                                          _stream(stream)))
+    return parent[: n_r + nn.value], label[: nn.value], nn.value, un.value
 
 
 TREE_NOALLOC_MAX = 1 << 18
@@ -541,15 +557,23 @@ def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: s
     """The whole exact path on device tensors: orientation, r-clique index, s-clique counts, peel
     and hierarchy.  method "el": link-efficient interleaved with the peel, then construct-tree
     (Alg. 3 + Alg. 5); "te": core numbers, then the two-phase hierarchy (§7.4, definitional
-    reading only); "auto": the builder measured faster on a GB300 (R-MAT 18, peel + hierarchy):
+    reading only); "bl": core numbers, then link-basic and construct-tree-basic (Alg. 4, the
+    ablation); "auto": the builder measured faster on a GB300 (R-MAT 18, peel + hierarchy):
     "te" for every pair but (3,4), whose linking peel is faster than its cores-only peel plus the
-    two-phase hierarchy; "el" for the pair rule (link_mode "pair"), which only "el" follows."""
+    two-phase hierarchy; "el" for the pair rule (link_mode "pair"), which only "el" follows.
+    Pairs beyond (1,2), (1,3), (2,3), (2,4), (3,4) (any r < s <= 7) run the generic path, where
+    "el" and "te" both link over every s-clique after the peel."""
     if method == "auto":
         method = "el" if (r, s) == (3, 4) or link_mode != "def" else "te"
     o = build_orientation(off, adj, stream)
     ri = index_r_cliques(o, r, stream)
     cnt, n_s = count_s_cliques(o, ri, s, stream=stream)
-    if method == "te":
+    if method == "bl":
+        assert link_mode == "def", "link-basic follows the definition here"
+        pk = peel_cores(o, ri, s, cnt, stats=stats, stream=stream)
+        parent, label, nn, unites = hierarchy_basic(o, ri, s, pk["core"], stream=stream)
+        pk["basic_unites"] = unites
+    elif method == "te":
         assert link_mode == "def", "the two-phase hierarchy follows the definition"
         pk = peel_cores(o, ri, s, cnt, stats=stats, stream=stream)
         parent, label, nn = hierarchy_two_phase(o, ri, s, pk["core"], stream=stream)
