@@ -521,23 +521,38 @@ def _cuda_timer(run) -> float:
     return a.elapsed_time(b)
 
 
-def autotune_peel(run, max_groups=(16, 64, 256, 1024), task_items=(-1,), repeats: int = 1,
+def set_relist_split(per_warp: float = 1.0, warp_grain: int = 128, block_grain: int = 1024, len_mult: int = 0):
+    """Sub-task size of the triangle-list re-listing ((2,4) without links): sub-tasks per warp of
+    the grid a round aims at, and the least scan bound of a warp / block sub-task; results never
+    depend on it."""
+    _check("nh_set_relist_split", lib().nh_set_relist_split(float(per_warp), int(warp_grain), int(block_grain),
+                                                            int(len_mult)))
+
+
+def autotune_peel(run, max_groups=(16, 64, 256, 1024), task_items=(-1,), splits=(None,), repeats: int = 1,
                   timer=None) -> dict:
     """Grid search over the peel's scheduling knobs: time `run()` (one piece of device work, e.g.
-    a whole hierarchy) under every (warps-per-r-clique cap, task-frontier size) pair, keep the
-    fastest pair set, and return {"best": (cap, items), "times_ms": {(cap, items): ms}}.  The knobs
-    change only the scheduling, never a result.  `timer(run) -> ms` defaults to CUDA events on
-    the current stream."""
+    a whole hierarchy) under every (warps-per-r-clique cap, task-frontier size[, sub-tasks per
+    warp]) combination, keep the fastest set, and return {"best": key, "times_ms": {key: ms}} with
+    key = (cap, items) or, when splits are given, (cap, items, split).  The knobs change only the
+    scheduling, never a result.  `timer(run) -> ms` defaults to CUDA events on the current
+    stream."""
     timer = timer or _cuda_timer
     times = {}
     for g in max_groups:
         for t in task_items:
-            set_peel_max_group(g)
-            set_peel_task_items(t)
-            times[(g, t)] = min(timer(run) for _ in range(max(1, repeats)))
+            for sp in splits:
+                set_peel_max_group(g)
+                set_peel_task_items(t)
+                if sp is not None:
+                    set_relist_split(sp)
+                key = (g, t) if sp is None else (g, t, sp)
+                times[key] = min(timer(run) for _ in range(max(1, repeats)))
     best = min(times, key=times.get)
     set_peel_max_group(best[0])
     set_peel_task_items(best[1])
+    if len(best) > 2:
+        set_relist_split(best[2])
     return {"best": best, "times_ms": times}
 
 

@@ -33,3 +33,15 @@ def test_autotune_max_group_wrapper(monkeypatch):
                                        timer=lambda run: {4: 2.0, 8: 1.0, 32: 1.5}[state["g"]])
     assert times == {4: 2.0, 8: 1.0, 32: 1.5}
     assert state["g"] == 8
+
+
+def test_autotune_three_knobs(monkeypatch):
+    state = {"g": None, "t": None, "sp": None}
+    monkeypatch.setattr(nc, "set_peel_max_group", lambda g: state.__setitem__("g", g))
+    monkeypatch.setattr(nc, "set_peel_task_items", lambda t: state.__setitem__("t", t))
+    monkeypatch.setattr(nc, "set_relist_split", lambda sp: state.__setitem__("sp", sp))
+    cost = lambda: {1: 3.0, 64: 2.0}[state["g"]] * {0.5: 1.0, 2.0: 0.5}[state["sp"]] + (state["t"] == 0)
+    res = nc.autotune_peel(lambda: None, max_groups=(1, 64), task_items=(0, -1), splits=(0.5, 2.0),
+                           timer=lambda run: cost())
+    assert res["best"] == (64, -1, 2.0) and state == {"g": 64, "t": -1, "sp": 2.0}
+    assert len(res["times_ms"]) == 8
