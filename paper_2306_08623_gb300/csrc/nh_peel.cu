@@ -31,6 +31,7 @@ extern long long g_nh_round_log_cap;
 static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
 static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
 static int g_peel_relist24 = 1;       // set by nh_set_peel_relist24
+static int g_peel_list_hash = 1;      // set by nh_set_peel_list_hash
 static float g_split_per_warp = 1.0f;  // set by nh_set_relist_split
 static int g_split_wgrain = 128, g_split_bgrain = 1024, g_split_len_mult = 0;
 
@@ -96,6 +97,55 @@ __global__ void k_max_u32(int64_t n, const uint32_t* __restrict__ a, unsigned in
 }
 
 // nh_link_pairs: one thread per call
+// (3,4): the (edge id, third vertex) -> list position table of the per-edge triangle lists
+__global__ void k_eh_fill(GView g, ulonglong2* __restrict__ eh, unsigned long long mask, int* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < g.m; e += nwarps) {
+    for (int64_t k = g.etoff[e] + lane; k < g.etoff[e + 1]; k += 32) {
+      const unsigned long long key = ((unsigned long long)(uint32_t)e << 32) | (uint32_t)g.etw[k];
+      unsigned long long h = nh_mix64(key) & mask;
+      bool done = false;
+      for (unsigned long long q = 0; q <= mask && !done; ++q) {
+        const unsigned long long old = atomicCAS(&eh[h].x, NH_EMPTY_KEY, key);
+        if (old == NH_EMPTY_KEY || old == key) {
+          eh[h].y = (unsigned long long)k;
+          done = true;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!done) atomicCAS(status, 0, NH_ERR_TABLE_FULL);
+    }
+  }
+}
+
+__global__ void k_eh_empty(ulonglong2* eh, unsigned long long cap) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    eh[i] = make_ulonglong2(NH_EMPTY_KEY, 0ull);
+}
+
+// Builds A.eh over the 3 n_r list entries when the knob is on and the table fits; otherwise
+// leaves A.eh null (binary searches).  status: device word for a full table.
+void build_list_hash(PeelArgs& A, int64_t n_r, int* status, ulonglong2** table, cudaStream_t st) {
+  *table = nullptr;
+  A.eh = nullptr;
+  if (!g_peel_list_hash || !A.et3) return;
+  unsigned long long cap = 1024;
+  while (cap < 2ull * 3ull * (unsigned long long)n_r) cap <<= 1;
+  if (nh_alloc(table, (int64_t)cap, st) != NH_OK) {
+    (void)cudaGetLastError();
+    *table = nullptr;
+    return;
+  }
+  k_eh_empty<<<nh_blocks_for((int64_t)cap, 256, 152 * 32), 256, 0, st>>>(*table, cap);
+  k_eh_fill<<<nh_blocks_for(A.g.m * 32, 256, 152 * 16), 256, 0, st>>>(A.g, *table, cap - 1, status);
+  nh_note_launch(2);
+  A.eh = *table;
+  A.eh_mask = cap - 1;
+}
+
 __global__ void k_link_pairs(LinkEnv E, const int2* __restrict__ pairs, unsigned long long n) {
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -217,6 +267,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   uint32_t* thr_dev = nullptr;
   unsigned int* dmax = nullptr;
   uint32_t* cost = nullptr;
+  ulonglong2* eh_table = nullptr;
   std::vector<uint32_t> thr_host;
   if ((rc = nh_alloc(&A.cnt, n_r, st)) || (rc = nh_alloc(&A.alive[0], n_r, st)) ||
       (rc = nh_alloc(&A.alive[1], n_r, st)) || (rc = nh_alloc(&A.front[0], n_r, st)) ||
@@ -284,6 +335,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   k_peel_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, cnt, A.cnt, round, val, A.alive[0],
                                                                   exact ? uf : nullptr, exact ? L : nullptr);
   nh_note_launch();
+  build_list_hash(A, n_r, &A.lk.ctl->err, &eh_table, st);
   if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
   rc = peel_launch_pair(r, s, exact, A, st);
   if (!rc && res_dev) {
@@ -315,7 +367,7 @@ cleanup:
   nh_free(A.front[1], st); nh_free(A.lk.ctl, st); nh_free(A.lk.ovf[0], st); nh_free(A.lk.ovf[1], st);
   nh_free(A.lk.cache, st); nh_free(A.lk.J, st);
   nh_free(thr_dev, st); nh_free(dmax, st); nh_free(cost, st); nh_free(A.c24_queue, st);
-  nh_free(A.et3, st); nh_free(A.tpos, st);
+  nh_free(A.et3, st); nh_free(A.tpos, st); nh_free(eh_table, st);
   if (res_dev) return (cudaGetLastError() != cudaSuccess && !rc) ? NH_ERR_CUDA : rc;
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
@@ -479,6 +531,7 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   int32_t* order = nullptr;
   uint32_t* cost = nullptr;
   uint32_t* mark = nullptr;
+  ulonglong2* eh_table = nullptr;
   int rc = NH_OK;
   unsigned int kmax = 0;
   if (label_mode) {
@@ -526,6 +579,7 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   cudaMemsetAsync(A.lk.ctl, 0, sizeof(PeelCtl), st);
   cudaMemsetAsync(A.touched_n, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(T.node_count, 0, sizeof(unsigned long long), st);
+  build_list_hash(A, n_r, &A.lk.ctl->err, &eh_table, st);
   T.order = order;
   T.lvl_off = off;
   T.kmax = kmax;
@@ -547,7 +601,7 @@ cleanup:
   nh_free(A.lk.uf, st); nh_free(A.lk.ctl, st); nh_free(A.touched, st); nh_free(A.touched_n, st);
   nh_free(T.lvl, st); nh_free(T.nid, st); nh_free(T.top, st); nh_free(T.node_count, st); nh_free(dmax, st);
   nh_free(order, st); nh_free(hist, st); nh_free(off, st); nh_free(cursor, st); nh_free(cost, st);
-  nh_free(mark, st); nh_free(A.c24_queue, st); nh_free(A.et3, st); nh_free(A.tpos, st);
+  nh_free(mark, st); nh_free(A.c24_queue, st); nh_free(A.et3, st); nh_free(A.tpos, st); nh_free(eh_table, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = NH_ERR_CUDA;
   return rc;
 }
@@ -565,6 +619,12 @@ extern "C" int nh_label_hierarchy(const nh_oriented* o, const nh_rindex* ri, int
 extern "C" int nh_set_peel_max_group(int g) {
   if (g < 1 || g > 1024 || (g & (g - 1))) return NH_ERR_INVALID;
   g_peel_max_group = g;
+  return NH_OK;
+}
+
+extern "C" int nh_set_peel_list_hash(int on) {
+  if (on != 0 && on != 1) return NH_ERR_INVALID;
+  g_peel_list_hash = on;
   return NH_OK;
 }
 

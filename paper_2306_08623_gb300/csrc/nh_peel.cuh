@@ -92,6 +92,8 @@ struct PeelArgs {
   int use24;              // (2,4) without links: re-list over the per-edge triangle lists
   int4* et3;              // (3,4): per-edge triangle lists with mirrored state, {w, triangle, stamp, value}
   int32_t* tpos;          //        the three list positions of every triangle (or null: plain lists)
+  const ulonglong2* eh;   // (3,4): {edge id << 32 | w, list position} of every list entry (or null:
+  unsigned long long eh_mask;  //   binary searches), open addressing at load <= 0.5
   unsigned long long* round_log;  // optional trace: per round (frontier << 32 | levels, end time)
   unsigned long long round_log_cap;
   unsigned long long* c24_queue;  // block queue of that re-listing (all ~0 between rounds)
@@ -811,22 +813,34 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
 #pragma unroll
           for (int i = 0; i < 3; i++) {
             if (i != bt && ok) {
-              int64_t lo = tl[i], hi = th[i];  // first entry with w' >= w
-              while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (__ldg(reinterpret_cast<const int32_t*>(A.et3 + mid)) < w) lo = mid + 1; else hi = mid;
-              }
-              ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps
-              if (lo < th[i]) {
-                const int4 f = __ldcg(A.et3 + lo);
-                if (f.x == w) {
-                  mem[i] = f.y;
-                  rdv[i] = (uint32_t)f.z;
-                  cv[i] = (uint32_t)f.w;
-                  ls.scan += 3;
-                } else {
-                  ok = false;
+              int64_t lo = -1;  // position of w in edge eR[i]'s list, or -1
+              if (A.eh) {
+                // one probe (a few on collisions) of the (edge, third vertex) table instead of a
+                // binary search of the list: a short chain of dependent loads
+                const unsigned long long key = ((unsigned long long)(uint32_t)eR[i] << 32) | (uint32_t)w;
+                unsigned long long h = nh_mix64(key) & A.eh_mask;
+                for (unsigned long long q = 0; q <= A.eh_mask; ++q) {
+                  const ulonglong2 sl = __ldg(A.eh + h);
+                  ++ls.probe;
+                  if (sl.x == key) { lo = (int64_t)sl.y; break; }
+                  if (sl.x == NH_EMPTY_KEY) break;
+                  h = (h + 1) & A.eh_mask;
                 }
+              } else {
+                int64_t a = tl[i], b = th[i];  // first entry with w' >= w
+                while (a < b) {
+                  const int64_t mid = (a + b) >> 1;
+                  if (__ldg(reinterpret_cast<const int32_t*>(A.et3 + mid)) < w) a = mid + 1; else b = mid;
+                }
+                ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps
+                if (a < th[i] && __ldg(reinterpret_cast<const int32_t*>(A.et3 + a)) == w) lo = a;
+              }
+              if (lo >= 0) {
+                const int4 f = __ldcg(A.et3 + lo);
+                mem[i] = f.y;
+                rdv[i] = (uint32_t)f.z;
+                cv[i] = (uint32_t)f.w;
+                ls.scan += 3;
               } else {
                 ok = false;
               }

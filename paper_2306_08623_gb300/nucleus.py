@@ -68,6 +68,7 @@ def lib():
             "nh_set_peel_max_group": (I32, [I32]),
             "nh_set_peel_task_items": (I32, [I32]),
             "nh_set_peel_relist24": (I32, [I32]),
+            "nh_set_peel_list_hash": (I32, [I32]),
             "nh_set_relist_split": (I32, [ctypes.c_float, I32, I32, I32]),
             "nh_debug_round_log": (I32, [P, I64]),
             "nh_approx_nucleus": (I32, [P, P, I32, ctypes.c_double, P, P, P, ctypes.POINTER(PeelStats), P]),
@@ -479,6 +480,12 @@ def set_peel_task_items(n: int):
     """Largest frontier (or level) re-listed as work-proportional chunk tasks (0..4096, 0 = off,
     -1 = automatic); results never depend on it."""
     _check("nh_set_peel_task_items", lib().nh_set_peel_task_items(int(n)))
+
+
+def set_peel_list_hash(on: bool):
+    """(3,4) re-listing: find a candidate's other two list entries through the (edge, third vertex)
+    table (True, the default) or by binary search (False); results never depend on it."""
+    _check("nh_set_peel_list_hash", lib().nh_set_peel_list_hash(int(bool(on))))
 
 
 def set_peel_relist24(on: bool):

@@ -253,9 +253,13 @@ def test_error_paths(nc):
     o = nc.build_orientation(d_off, d_adj)
     ri = nc.index_r_cliques(o, 2)
     cnt, _ = nc.count_s_cliques(o, ri, 3)
+    for bad_s in (8, 2, 1):  # s beyond 7, or not above r
+        with pytest.raises(nc.NucleusError) as e:
+            nc.count_s_cliques(o, ri, bad_s)
+        assert e.value.status == 6
     with pytest.raises(nc.NucleusError) as e:
-        nc.count_s_cliques(o, ri, 5)
-    assert e.value.status == 6
+        nc.index_r_cliques(o, 7)  # r-clique index: r <= 6
+    assert e.value.status == 1
     with pytest.raises(nc.NucleusError) as e:
         nc.approx_nucleus(o, ri, 3, -1.0, cnt)
     assert e.value.status == 1

@@ -87,6 +87,18 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     assert np.array_equal(h["core"], g["core"]) and np.array_equal(h["round"], g["round"])
     for d in (0.1, 0.5):
         assert np.array_equal(h["approx_%g" % d], g["approx_%g" % d])
+    if (r, s) == (3, 4):
+        # binary searches of the lists in place of the (edge, third vertex) table: the same results
+        nc.set_peel_list_hash(False)
+        try:
+            b = _run(nc, off, adj, r, s, True)
+        finally:
+            nc.set_peel_list_hash(True)
+        assert np.array_equal(b["core"], g["core"]) and np.array_equal(b["round"], g["round"])
+        compare_hierarchy(b["parent"], b["label"], b["nn"], ref["leaf_node"], ref["node_parent"], ref["node_label"])
+        for d in (0.1, 0.5):
+            assert np.array_equal(b["approx_%g" % d], g["approx_%g" % d])
+        assert g["stats"]["hash_probes"] > 0 and b["stats"]["hash_probes"] == 0
 
 
 def test_long_lists_take_every_branch(nc):
@@ -102,3 +114,5 @@ def test_long_lists_take_every_branch(nc):
 def test_relist24_knob_rejects_bad_values(nc):
     assert nc.lib().nh_set_peel_relist24(2) == 1
     assert nc.lib().nh_set_peel_relist24(1) == 0
+    assert nc.lib().nh_set_peel_list_hash(2) == 1
+    assert nc.lib().nh_set_peel_list_hash(1) == 0
