@@ -18,6 +18,8 @@ from paper_2306_08623_gb300 import graphgen as gg
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 RS_SMALL = [(1, 2), (1, 3), (2, 3), (1, 4), (2, 4), (3, 4), (2, 5), (3, 5)]
+# every other r < s <= 7 (the generic GPU path's pairs), with fewer trials each
+RS_WIDE = [(r, s) for s in range(5, 8) for r in range(1, s) if (r, s) not in RS_SMALL]
 
 
 def _gold(name):
@@ -54,6 +56,39 @@ def test_oracle_vs_brute_force(r, s):
         assert _hier(oracle.nucleus(off, adj, r, s, hier="pair")) == bp["nodes"], (n, edges)
         assert _hier(oracle.nucleus(off, adj, r, s, hier="link_def")) == bf["nodes"], (n, edges)
         assert _hier(oracle.nucleus(off, adj, r, s, hier="link_pair")) == bp["nodes"], (n, edges)
+
+
+@pytest.mark.parametrize("r,s", RS_WIDE)
+def test_oracle_vs_brute_force_wide_pairs(r, s):
+    """The same pins for the remaining pairs up to s = 7 on graphs with planted overlapping cliques
+    (so that s-cliques and nuclei of several levels exist): tuples, counts, core numbers, both
+    hierarchy readings, both hierarchy algorithms."""
+    rng = np.random.default_rng(500 + 10 * r + s)
+    with_nodes = 0
+    for trial in range(12):
+        # two or three overlapping planted cliques of s..s+2 vertices plus sparse random edges:
+        # nuclei of several levels
+        n = int(rng.integers(s + 2, 14))
+        es = set()
+        for _ in range(int(rng.integers(2, 4))):
+            k = int(rng.integers(s, min(s + 3, n + 1)))
+            vs = sorted(rng.choice(n, size=k, replace=False).tolist())
+            es |= {(a, b) for i, a in enumerate(vs) for b in vs[i + 1:]}
+        es |= {(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.25}
+        off, adj = gg.from_edges(n, sorted(es))
+        edges = [tuple(e) for e in gg.edge_list(off, adj)]
+        bf = brute_nucleus(n, edges, r, s, "def")
+        bp = brute_nucleus(n, edges, r, s, "pair")
+        res = oracle.nucleus(off, adj, r, s, hier="def")
+        assert [tuple(t) for t in res["tuples"]] == bf["rcliques"]
+        assert res["n_s"] == bf["n_s"]
+        assert res["cnt"].tolist() == bf["cnt"]
+        assert res["core"].tolist() == bf["core"], (n, edges)
+        assert _hier(res) == bf["nodes"], (n, edges)
+        assert _hier(oracle.nucleus(off, adj, r, s, hier="pair")) == bp["nodes"], (n, edges)
+        assert _hier(oracle.nucleus(off, adj, r, s, hier="link_def")) == bf["nodes"], (n, edges)
+        with_nodes += len(bf["nodes"]) > 1
+    assert with_nodes >= 3  # the pins are not vacuous: several trials have multi-node hierarchies
 
 
 def test_level_and_link_hierarchies_agree_medium():
