@@ -31,7 +31,7 @@ extern long long g_nh_round_log_cap;
 static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
 static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
 static int g_peel_relist24 = 1;       // set by nh_set_peel_relist24
-static int g_peel_list_hash = 1;      // set by nh_set_peel_list_hash
+static int g_peel_list_hash = 1;      // set by nh_set_peel_list_hash (0 off, 1 automatic, 2 always)
 static float g_split_per_warp = 1.0f;  // set by nh_set_relist_split
 static int g_split_wgrain = 128, g_split_bgrain = 1024, g_split_len_mult = 0;
 
@@ -126,14 +126,18 @@ __global__ void k_eh_empty(ulonglong2* eh, unsigned long long cap) {
     eh[i] = make_ulonglong2(NH_EMPTY_KEY, 0ull);
 }
 
-// Builds A.eh over the 3 n_r list entries when the knob is on and the table fits; otherwise
-// leaves A.eh null (binary searches).  status: device word for a full table.
-void build_list_hash(PeelArgs& A, int64_t n_r, int* status, ulonglong2** table, cudaStream_t st) {
+// Builds A.eh over the 3 n_r list entries when the knob asks for it and the table fits;
+// otherwise leaves A.eh null (binary searches).  Automatic (knob 1): only for the peels that
+// prune candidates before the lookups (cores only, approximate) -- measured on R-MAT 18 (3,4):
+// cores-only peel 1132 -> 1090 ms, but the linking peel, which looks up every candidate, 2027 ->
+// 2305 ms and the two-phase hierarchy 913 -> 927 ms (the list searches stay in cache, the table's
+// slots do not).  status: device word for a full table.
+void build_list_hash(PeelArgs& A, int64_t n_r, bool pruned, int* status, ulonglong2** table, cudaStream_t st) {
   *table = nullptr;
   A.eh = nullptr;
-  if (!g_peel_list_hash || !A.et3) return;
+  if (!A.et3 || g_peel_list_hash == 0 || (g_peel_list_hash == 1 && !pruned)) return;
   unsigned long long cap = 1024;
-  while (cap < 2ull * 3ull * (unsigned long long)n_r) cap <<= 1;
+  while (cap < 5ull * (unsigned long long)n_r) cap <<= 1;  // 3 n_r entries at load <= 0.6
   if (nh_alloc(table, (int64_t)cap, st) != NH_OK) {
     (void)cudaGetLastError();
     *table = nullptr;
@@ -335,7 +339,7 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
   k_peel_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, cnt, A.cnt, round, val, A.alive[0],
                                                                   exact ? uf : nullptr, exact ? L : nullptr);
   nh_note_launch();
-  build_list_hash(A, n_r, &A.lk.ctl->err, &eh_table, st);
+  build_list_hash(A, n_r, !exact || link_mode == 2, &A.lk.ctl->err, &eh_table, st);
   if (cudaGetLastError() != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
   rc = peel_launch_pair(r, s, exact, A, st);
   if (!rc && res_dev) {
@@ -579,7 +583,7 @@ static int two_phase_impl(const nh_oriented* o, const nh_rindex* ri, int s, cons
   cudaMemsetAsync(A.lk.ctl, 0, sizeof(PeelCtl), st);
   cudaMemsetAsync(A.touched_n, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(T.node_count, 0, sizeof(unsigned long long), st);
-  build_list_hash(A, n_r, &A.lk.ctl->err, &eh_table, st);
+  build_list_hash(A, n_r, false, &A.lk.ctl->err, &eh_table, st);
   T.order = order;
   T.lvl_off = off;
   T.kmax = kmax;
@@ -622,9 +626,9 @@ extern "C" int nh_set_peel_max_group(int g) {
   return NH_OK;
 }
 
-extern "C" int nh_set_peel_list_hash(int on) {
-  if (on != 0 && on != 1) return NH_ERR_INVALID;
-  g_peel_list_hash = on;
+extern "C" int nh_set_peel_list_hash(int mode) {
+  if (mode < 0 || mode > 2) return NH_ERR_INVALID;
+  g_peel_list_hash = mode;
   return NH_OK;
 }
 

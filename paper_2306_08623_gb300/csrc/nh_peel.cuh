@@ -796,58 +796,81 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
     if (th[2] - tl[2] < th[bt] - tl[bt]) bt = 2;
     if (A.et3) {
       // mirrored lists: an entry holds its triangle's round stamp and value, so a search hit
-      // brings everything the s-clique needs in one sector
-      if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(4 * (th[bt] - tl[bt]));
-      for (int64_t c = c0; c < cend && tl[bt] + 32 * c < th[bt]; c += cstep) {
-        const int64_t j = tl[bt] + 32 * c + lane;
-        bool ok = j < th[bt];
-        int32_t mem[3] = {0, 0, 0};
-        uint32_t rdv[3] = {0, 0, 0}, cv[3] = {0, 0, 0};
+      // brings everything the s-clique needs in one sector.  The scanned list (edge bt) and the
+      // other two (i0 < i1) are taken apart into scalars so that nothing is indexed at run time.
+      const int64_t lb = (bt == 0) ? tl[0] : (bt == 1) ? tl[1] : tl[2];
+      const int64_t hb = (bt == 0) ? th[0] : (bt == 1) ? th[1] : th[2];
+      const int64_t l0 = (bt == 0) ? tl[1] : tl[0], h0 = (bt == 0) ? th[1] : th[0];
+      const int64_t l1 = (bt == 2) ? tl[1] : tl[2], h1 = (bt == 2) ? th[1] : th[2];
+      const int32_t e0 = (bt == 0) ? eR[1] : eR[0], e1 = (bt == 2) ? eR[1] : eR[2];
+      if (lane == 0 && c0 == 0 && se == 0) ls.scan += (unsigned long long)(4 * (hb - lb));
+      for (int64_t c = c0; c < cend && lb + 32 * c < hb; c += cstep) {
+        const int64_t j = lb + 32 * c + lane;
+        bool ok = j < hb;
+        int4 en = make_int4(0, 0, 0, 0), f0 = en, f1 = en;
         if (ok) {
-          const int4 en = __ldcg(A.et3 + j);
+          en = __ldcg(A.et3 + j);
           const int32_t w = en.x;
-          mem[bt] = en.y;
-          rdv[bt] = (uint32_t)en.z;
-          cv[bt] = (uint32_t)en.w;
-          ok = member_may_count_v(A, Rid, en.y, rdv[bt], cv[bt], t, thr);
-#pragma unroll
-          for (int i = 0; i < 3; i++) {
-            if (i != bt && ok) {
-              int64_t lo = -1;  // position of w in edge eR[i]'s list, or -1
-              if (A.eh) {
-                // one probe (a few on collisions) of the (edge, third vertex) table instead of a
-                // binary search of the list: a short chain of dependent loads
-                const unsigned long long key = ((unsigned long long)(uint32_t)eR[i] << 32) | (uint32_t)w;
-                unsigned long long h = nh_mix64(key) & A.eh_mask;
-                for (unsigned long long q = 0; q <= A.eh_mask; ++q) {
-                  const ulonglong2 sl = __ldg(A.eh + h);
+          ok = member_may_count_v(A, Rid, en.y, (uint32_t)en.z, (uint32_t)en.w, t, thr);
+          if (ok) {
+            // w's entries in the other two lists: both lookups advance in the same loop, so that
+            // each lane has two independent loads in flight and the chain of dependent loads is
+            // that of one lookup, not two
+            int64_t p0 = -1, p1 = -1;
+            if (A.eh) {
+              const unsigned long long k0 = ((unsigned long long)(uint32_t)e0 << 32) | (uint32_t)w;
+              const unsigned long long k1 = ((unsigned long long)(uint32_t)e1 << 32) | (uint32_t)w;
+              unsigned long long q0 = nh_mix64(k0) & A.eh_mask, q1 = nh_mix64(k1) & A.eh_mask;
+              bool d0 = false, d1 = false;
+              for (unsigned long long q = 0; q <= A.eh_mask && !(d0 && d1); ++q) {
+                const ulonglong2 s0 = d0 ? make_ulonglong2(0ull, 0ull) : __ldg(A.eh + q0);
+                const ulonglong2 s1 = d1 ? make_ulonglong2(0ull, 0ull) : __ldg(A.eh + q1);
+                if (!d0) {
                   ++ls.probe;
-                  if (sl.x == key) { lo = (int64_t)sl.y; break; }
-                  if (sl.x == NH_EMPTY_KEY) break;
-                  h = (h + 1) & A.eh_mask;
+                  if (s0.x == k0) { p0 = (int64_t)s0.y; d0 = true; }
+                  else if (s0.x == NH_EMPTY_KEY) d0 = true;
+                  else q0 = (q0 + 1) & A.eh_mask;
                 }
-              } else {
-                int64_t a = tl[i], b = th[i];  // first entry with w' >= w
-                while (a < b) {
-                  const int64_t mid = (a + b) >> 1;
-                  if (__ldg(reinterpret_cast<const int32_t*>(A.et3 + mid)) < w) a = mid + 1; else b = mid;
+                if (!d1) {
+                  ++ls.probe;
+                  if (s1.x == k1) { p1 = (int64_t)s1.y; d1 = true; }
+                  else if (s1.x == NH_EMPTY_KEY) d1 = true;
+                  else q1 = (q1 + 1) & A.eh_mask;
                 }
-                ls.scan += 65 - __clzll((unsigned long long)(th[i] - tl[i]));  // search steps
-                if (a < th[i] && __ldg(reinterpret_cast<const int32_t*>(A.et3 + a)) == w) lo = a;
               }
-              if (lo >= 0) {
-                const int4 f = __ldcg(A.et3 + lo);
-                mem[i] = f.y;
-                rdv[i] = (uint32_t)f.z;
-                cv[i] = (uint32_t)f.w;
-                ls.scan += 3;
-              } else {
-                ok = false;
+            } else {
+              // first entries with w' >= w in both lists, searched in lockstep
+              int64_t a0 = l0, b0 = h0, a1 = l1, b1 = h1;
+              ls.scan += (65 - __clzll((unsigned long long)(h0 - l0))) + (65 - __clzll((unsigned long long)(h1 - l1)));
+              while (a0 < b0 || a1 < b1) {
+                const int64_t m0 = (a0 + b0) >> 1, m1 = (a1 + b1) >> 1;
+                const int32_t x0 = (a0 < b0) ? __ldg(reinterpret_cast<const int32_t*>(A.et3 + m0)) : 0;
+                const int32_t x1 = (a1 < b1) ? __ldg(reinterpret_cast<const int32_t*>(A.et3 + m1)) : 0;
+                if (a0 < b0) { if (x0 < w) a0 = m0 + 1; else b0 = m0; }
+                if (a1 < b1) { if (x1 < w) a1 = m1 + 1; else b1 = m1; }
               }
+              p0 = a0;
+              p1 = a1;
+            }
+            ok = p0 >= 0 && p1 >= 0 && p0 < h0 && p1 < h1;
+            if (ok) {
+              f0 = __ldcg(A.et3 + p0);
+              f1 = __ldcg(A.et3 + p1);
+              ok = f0.x == w && f1.x == w;
+              if (ok) ls.scan += 6;
             }
           }
         }
-        if (ok) process_S_pre<3, EXACT>(A, Rid, mem, rdv, cv, t, thr, nf, W, ls);
+        if (ok) {
+          // members in edge order: the scanned list's triangle at bt, the others at i0 < i1
+          const int32_t mem[3] = {bt == 0 ? en.y : f0.y, bt == 1 ? en.y : (bt == 0 ? f0.y : f1.y),
+                                  bt == 2 ? en.y : f1.y};
+          const uint32_t rdv[3] = {(uint32_t)(bt == 0 ? en.z : f0.z), (uint32_t)(bt == 1 ? en.z : (bt == 0 ? f0.z : f1.z)),
+                                   (uint32_t)(bt == 2 ? en.z : f1.z)};
+          const uint32_t cv[3] = {(uint32_t)(bt == 0 ? en.w : f0.w), (uint32_t)(bt == 1 ? en.w : (bt == 0 ? f0.w : f1.w)),
+                                  (uint32_t)(bt == 2 ? en.w : f1.w)};
+          process_S_pre<3, EXACT>(A, Rid, mem, rdv, cv, t, thr, nf, W, ls);
+        }
         if constexpr (EXACT) wl_maybe_flush(W, A, Rid, lane, kPerLane, ls);
       }
       return;

@@ -482,10 +482,11 @@ def set_peel_task_items(n: int):
     _check("nh_set_peel_task_items", lib().nh_set_peel_task_items(int(n)))
 
 
-def set_peel_list_hash(on: bool):
-    """(3,4) re-listing: find a candidate's other two list entries through the (edge, third vertex)
-    table (True, the default) or by binary search (False); results never depend on it."""
-    _check("nh_set_peel_list_hash", lib().nh_set_peel_list_hash(int(bool(on))))
+def set_peel_list_hash(mode: int):
+    """(3,4) re-listing: find a candidate's other two list entries by binary search (0), through
+    the (edge, third vertex) table (2), or automatically (1, the default: the table for the
+    cores-only and approximate peels); results never depend on it."""
+    _check("nh_set_peel_list_hash", lib().nh_set_peel_list_hash(int(mode)))
 
 
 def set_peel_relist24(on: bool):

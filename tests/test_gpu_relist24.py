@@ -75,11 +75,12 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     ec, ep, elab, enn = g["el"]
     assert np.array_equal(ec, ref["core"])
     compare_hierarchy(ep, elab, enn, ref["leaf_node"], ref["node_parent"], ref["node_label"])
+    rls = {}
     for d in (0.1, 0.5):
         ra = oracle.nucleus(off, adj, r, s, hier=None, approx_delta=d)
         assert np.array_equal(g["approx_%g" % d], ra["approx"]), d
         assert g["approx_rounds_%g" % d] == ra["approx_rounds"]
-        rl = oracle.label_hierarchy(off, adj, r, s, g["approx_%g" % d])
+        rl = rls[d] = oracle.label_hierarchy(off, adj, r, s, g["approx_%g" % d])
         lp, ll, ln = g["lab_%g" % d]
         compare_hierarchy(lp, ll, ln, rl["leaf_node"], rl["node_parent"], rl["node_label"])
     # the other re-listing gives the same round stamps (the peel is round-synchronous)
@@ -88,17 +89,26 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     for d in (0.1, 0.5):
         assert np.array_equal(h["approx_%g" % d], g["approx_%g" % d])
     if (r, s) == (3, 4):
-        # binary searches of the lists in place of the (edge, third vertex) table: the same results
-        nc.set_peel_list_hash(False)
-        try:
-            b = _run(nc, off, adj, r, s, True)
-        finally:
-            nc.set_peel_list_hash(True)
-        assert np.array_equal(b["core"], g["core"]) and np.array_equal(b["round"], g["round"])
-        compare_hierarchy(b["parent"], b["label"], b["nn"], ref["leaf_node"], ref["node_parent"], ref["node_label"])
-        for d in (0.1, 0.5):
-            assert np.array_equal(b["approx_%g" % d], g["approx_%g" % d])
-        assert g["stats"]["hash_probes"] > 0 and b["stats"]["hash_probes"] == 0
+        # binary searches everywhere (0) and the (edge, third vertex) table everywhere (2) in place
+        # of the automatic choice: the same results, the linking peel and the hierarchies included
+        for mode in (0, 2):
+            nc.set_peel_list_hash(mode)
+            try:
+                b = _run(nc, off, adj, r, s, True)
+            finally:
+                nc.set_peel_list_hash(1)
+            assert np.array_equal(b["core"], g["core"]) and np.array_equal(b["round"], g["round"])
+            compare_hierarchy(b["parent"], b["label"], b["nn"], ref["leaf_node"], ref["node_parent"],
+                              ref["node_label"])
+            ec, ep, elab, enn = b["el"]
+            assert np.array_equal(ec, ref["core"])
+            compare_hierarchy(ep, elab, enn, ref["leaf_node"], ref["node_parent"], ref["node_label"])
+            for d in (0.1, 0.5):
+                assert np.array_equal(b["approx_%g" % d], g["approx_%g" % d])
+                lp, ll, ln = b["lab_%g" % d]
+                compare_hierarchy(lp, ll, ln, rls[d]["leaf_node"], rls[d]["node_parent"], rls[d]["node_label"])
+            assert (b["stats"]["hash_probes"] > 0) == (mode == 2)
+        assert g["stats"]["hash_probes"] > 0  # the cores-only peel takes the table automatically
 
 
 def test_long_lists_take_every_branch(nc):
@@ -114,5 +124,6 @@ def test_long_lists_take_every_branch(nc):
 def test_relist24_knob_rejects_bad_values(nc):
     assert nc.lib().nh_set_peel_relist24(2) == 1
     assert nc.lib().nh_set_peel_relist24(1) == 0
-    assert nc.lib().nh_set_peel_list_hash(2) == 1
+    assert nc.lib().nh_set_peel_list_hash(3) == 1
+    assert nc.lib().nh_set_peel_list_hash(-1) == 1
     assert nc.lib().nh_set_peel_list_hash(1) == 0
