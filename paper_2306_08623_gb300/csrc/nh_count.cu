@@ -31,6 +31,41 @@ __device__ __forceinline__ void tri_add(const GView& g, unsigned long long key, 
   cnt_add(cnt, id, inc, status);
 }
 
+// Three independent triangle-id look-ups advanced in lockstep (linear probing, each capped at the
+// table size): every probe round issues up to three independent loads, so the chain of dependent
+// loads is that of one look-up, not three.  A key that is absent sets NH_ERR_INTERNAL.
+__device__ __forceinline__ void tri_add3(const GView& g, unsigned long long k0, unsigned long long k1,
+                                         unsigned long long k2, uint32_t* cnt, int* status) {
+  const unsigned long long m = g.mask;
+  unsigned long long h0 = nh_mix64(k0) & m, h1 = nh_mix64(k1) & m, h2 = nh_mix64(k2) & m;
+  int64_t i0 = -1, i1 = -1, i2 = -1;
+  bool d0 = false, d1 = false, d2 = false;
+  for (unsigned long long q = 0; q <= m && !(d0 && d1 && d2); ++q) {
+    const ulonglong2 s0 = d0 ? make_ulonglong2(0ull, 0ull) : __ldg(reinterpret_cast<const ulonglong2*>(g.table + h0));
+    const ulonglong2 s1 = d1 ? make_ulonglong2(0ull, 0ull) : __ldg(reinterpret_cast<const ulonglong2*>(g.table + h1));
+    const ulonglong2 s2 = d2 ? make_ulonglong2(0ull, 0ull) : __ldg(reinterpret_cast<const ulonglong2*>(g.table + h2));
+    if (!d0) {
+      if (s0.x == k0) { i0 = (int64_t)(uint32_t)s0.y; d0 = true; }
+      else if (s0.x == NH_EMPTY_KEY) d0 = true;
+      else h0 = (h0 + 1) & m;
+    }
+    if (!d1) {
+      if (s1.x == k1) { i1 = (int64_t)(uint32_t)s1.y; d1 = true; }
+      else if (s1.x == NH_EMPTY_KEY) d1 = true;
+      else h1 = (h1 + 1) & m;
+    }
+    if (!d2) {
+      if (s2.x == k2) { i2 = (int64_t)(uint32_t)s2.y; d2 = true; }
+      else if (s2.x == NH_EMPTY_KEY) d2 = true;
+      else h2 = (h2 + 1) & m;
+    }
+  }
+  if (i0 < 0 || i1 < 0 || i2 < 0) { atomicExch(status, NH_ERR_INTERNAL); return; }
+  cnt_add(cnt, i0, 1u, status);
+  cnt_add(cnt, i1, 1u, status);
+  cnt_add(cnt, i2, 1u, status);
+}
+
 // (1,2): the s-clique-degree of a vertex is its degree
 __global__ void k_count_12(int64_t n, const int64_t* __restrict__ off, uint32_t* __restrict__ cnt) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
@@ -183,11 +218,9 @@ __global__ void k_count_s4(GView g, uint32_t* __restrict__ cnt, unsigned long lo
         const int32_t e_vc = c2e1[k], e_ac = c2e2[k], e_bc = g.oeid[j];
         if (R == 1) cnt_add(cnt, c, 1u, status);
         if (R == 2) { cnt_add(cnt, e_vc, 1u, status); cnt_add(cnt, e_ac, 1u, status); cnt_add(cnt, e_bc, 1u, status); }
-        if (R == 3) {
-          tri_add(g, nh_tri_key(v, a, c, e_va, e_vc, e_ac), 1u, cnt, status);
-          tri_add(g, nh_tri_key(v, b, c, e_vb, e_vc, e_bc), 1u, cnt, status);
-          tri_add(g, nh_tri_key(a, b, c, e_ab, e_ac, e_bc), 1u, cnt, status);
-        }
+        if (R == 3)
+          tri_add3(g, nh_tri_key(v, a, c, e_va, e_vc, e_ac), nh_tri_key(v, b, c, e_vb, e_vc, e_bc),
+                   nh_tri_key(a, b, c, e_ab, e_ac, e_bc), cnt, status);
       }
       n3 = warp_sum(n3);
       if (lane == 0 && n3) {
