@@ -839,13 +839,15 @@ __device__ __forceinline__ void relist_item(const PeelArgs& A, int32_t Rid, uint
                 }
               }
             } else {
-              // first entries with w' >= w in both lists, searched in lockstep
+              // first entries with w' >= w in both lists, searched in lockstep over the compact
+              // third-vertex array (4-byte entries: the last five steps of a search stay within
+              // one 128-byte line) rather than the 16-byte mirrored entries
               int64_t a0 = l0, b0 = h0, a1 = l1, b1 = h1;
               ls.scan += (65 - __clzll((unsigned long long)(h0 - l0))) + (65 - __clzll((unsigned long long)(h1 - l1)));
               while (a0 < b0 || a1 < b1) {
                 const int64_t m0 = (a0 + b0) >> 1, m1 = (a1 + b1) >> 1;
-                const int32_t x0 = (a0 < b0) ? __ldg(reinterpret_cast<const int32_t*>(A.et3 + m0)) : 0;
-                const int32_t x1 = (a1 < b1) ? __ldg(reinterpret_cast<const int32_t*>(A.et3 + m1)) : 0;
+                const int32_t x0 = (a0 < b0) ? __ldg(g.etw + m0) : 0;
+                const int32_t x1 = (a1 < b1) ? __ldg(g.etw + m1) : 0;
                 if (a0 < b0) { if (x0 < w) a0 = m0 + 1; else b0 = m0; }
                 if (a1 < b1) { if (x1 < w) a1 = m1 + 1; else b1 = m1; }
               }
