@@ -330,14 +330,15 @@ int nh_set_peel_task_items(int n);
  * NH_ERR_INVALID for other values. */
 int nh_set_peel_relist24(int on);
 
-/* Tuning knob (process-wide, default 1) of the (3,4) re-listing over the mirrored triangle lists:
+/* Tuning knob (process-wide, default 0) of the (3,4) re-listing over the mirrored triangle lists:
  * how a candidate's entries in its other two triangle lists are found.  mode = 0: binary searches
  * of the lists (both lists searched in lockstep); 2: a table keyed by (edge id, third vertex)
  * built for the call (16-byte slots, at most 60 % full: 48 to 128 bytes per triangle of extra
  * working memory; skipped when it cannot be allocated); 1 (automatic): the table for the
  * cores-only and the approximate peel, whose candidates are pruned before the lookups, binary
- * searches for the linking peel and the two-phase hierarchy.  Results never depend on it.
- * NH_ERR_INVALID for other values. */
+ * searches for the linking peel and the two-phase hierarchy.  On R-MAT 18 (3,4) the searches are
+ * as fast as the table for the cores-only peel and faster elsewhere, hence the default 0.
+ * Results never depend on it.  NH_ERR_INVALID for other values. */
 int nh_set_peel_list_hash(int mode);
 
 /* Tuning knob of that (2,4) re-listing (process-wide): a frontier (or level) of at most 4096

@@ -31,7 +31,7 @@ extern long long g_nh_round_log_cap;
 static int g_peel_max_group = 1024;   // set by nh_set_peel_max_group
 static int g_peel_task_items = -1;    // set by nh_set_peel_task_items (-1: automatic)
 static int g_peel_relist24 = 1;       // set by nh_set_peel_relist24
-static int g_peel_list_hash = 1;      // set by nh_set_peel_list_hash (0 off, 1 automatic, 2 always)
+static int g_peel_list_hash = 0;      // set by nh_set_peel_list_hash (0 off, 1 automatic, 2 always)
 static float g_split_per_warp = 1.0f;  // set by nh_set_relist_split
 static int g_split_wgrain = 128, g_split_bgrain = 1024, g_split_len_mult = 0;
 
@@ -128,10 +128,11 @@ __global__ void k_eh_empty(ulonglong2* eh, unsigned long long cap) {
 
 // Builds A.eh over the 3 n_r list entries when the knob asks for it and the table fits;
 // otherwise leaves A.eh null (binary searches).  Automatic (knob 1): only for the peels that
-// prune candidates before the lookups (cores only, approximate) -- measured on R-MAT 18 (3,4):
-// cores-only peel 1132 -> 1090 ms, but the linking peel, which looks up every candidate, 2027 ->
-// 2305 ms and the two-phase hierarchy 913 -> 927 ms (the list searches stay in cache, the table's
-// slots do not).  status: device word for a full table.
+// prune candidates before the lookups (cores only, approximate).  Measured on R-MAT 18 (3,4) with
+// the searches over the compact third-vertex array: cores-only peel 1100 ms searching, 1098 ms
+// with the table; linking peel 1992 vs 2301 ms; two-phase hierarchy 897 vs 927 ms (the list
+// searches stay in cache, the table's slots do not), so the default (knob 0) searches.
+// status: device word for a full table.
 void build_list_hash(PeelArgs& A, int64_t n_r, bool pruned, int* status, ulonglong2** table, cudaStream_t st) {
   *table = nullptr;
   A.eh = nullptr;

@@ -483,8 +483,8 @@ def set_peel_task_items(n: int):
 
 
 def set_peel_list_hash(mode: int):
-    """(3,4) re-listing: find a candidate's other two list entries by binary search (0), through
-    the (edge, third vertex) table (2), or automatically (1, the default: the table for the
+    """(3,4) re-listing: find a candidate's other two list entries by binary search (0, the
+    default), through the (edge, third vertex) table (2), or automatically (1: the table for the
     cores-only and approximate peels); results never depend on it."""
     _check("nh_set_peel_list_hash", lib().nh_set_peel_list_hash(int(mode)))
 

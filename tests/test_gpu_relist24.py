@@ -89,14 +89,15 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
     for d in (0.1, 0.5):
         assert np.array_equal(h["approx_%g" % d], g["approx_%g" % d])
     if (r, s) == (3, 4):
-        # binary searches everywhere (0) and the (edge, third vertex) table everywhere (2) in place
-        # of the automatic choice: the same results, the linking peel and the hierarchies included
-        for mode in (0, 2):
+        # the (edge, third vertex) table for the pruned peels (1) and everywhere (2) in place of
+        # the default binary searches: the same results, the linking peel and the hierarchies
+        # included
+        for mode in (1, 2):
             nc.set_peel_list_hash(mode)
             try:
                 b = _run(nc, off, adj, r, s, True)
             finally:
-                nc.set_peel_list_hash(1)
+                nc.set_peel_list_hash(0)
             assert np.array_equal(b["core"], g["core"]) and np.array_equal(b["round"], g["round"])
             compare_hierarchy(b["parent"], b["label"], b["nn"], ref["leaf_node"], ref["node_parent"],
                               ref["node_label"])
@@ -107,8 +108,8 @@ def test_triangle_list_relisting_matches_oracle(nc, name, r, s):
                 assert np.array_equal(b["approx_%g" % d], g["approx_%g" % d])
                 lp, ll, ln = b["lab_%g" % d]
                 compare_hierarchy(lp, ll, ln, rls[d]["leaf_node"], rls[d]["node_parent"], rls[d]["node_label"])
-            assert (b["stats"]["hash_probes"] > 0) == (mode == 2)
-        assert g["stats"]["hash_probes"] > 0  # the cores-only peel takes the table automatically
+            assert b["stats"]["hash_probes"] > 0  # the cores-only peel takes the table in both modes
+        assert g["stats"]["hash_probes"] == 0
 
 
 def test_long_lists_take_every_branch(nc):
@@ -127,3 +128,4 @@ def test_relist24_knob_rejects_bad_values(nc):
     assert nc.lib().nh_set_peel_list_hash(3) == 1
     assert nc.lib().nh_set_peel_list_hash(-1) == 1
     assert nc.lib().nh_set_peel_list_hash(1) == 0
+    assert nc.lib().nh_set_peel_list_hash(0) == 0  # back to the default
