@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
-    ap.add_argument("--workload", choices=["rmat18", "cl4m", "batch512", "approx", "approx_hier", "peel1"],
+    ap.add_argument("--workload", choices=["rmat18", "er2k", "cl4m", "batch512", "approx", "approx_hier", "peel1"],
                     default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
@@ -444,7 +444,8 @@ def run_ours(args):
         del flush
         torch.cuda.empty_cache()
         extras = {}
-        for name, fn in (("cl4m", measure_cl4m), ("batch512", measure_batch512), ("approx", measure_approx)):
+        for name, fn in (("er2k", measure_er2k), ("cl4m", measure_cl4m), ("batch512", measure_batch512),
+                         ("approx", measure_approx)):
             t0 = time.perf_counter()
             try:
                 extras[name] = fn()
@@ -524,6 +525,60 @@ def _ms(a, b):
 def _spread(xs):
     import numpy as np
     return {"median": float(np.median(xs)), "min": float(np.min(xs)), "max": float(np.max(xs)), "n": len(xs)}
+
+
+def measure_er2k(warmup: int = 3, steps: int = 20) -> dict:
+    """Erdos-Renyi G(n=2000, m=16000), seed 1: the exact (2,3) hierarchy as a latency workload.
+    Eager: the whole path through the binding (orientation, index, count, peel, tree); graph: the
+    count -> peel -> tree sequence (nh_hierarchy_enqueue) on a prepared orientation and index,
+    replayed from a CUDA graph.  Core numbers and the canonical hierarchy are compared with the
+    oracle's for the same graph, which is also timed (one host thread)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    off, adj = gg.erdos_renyi(2000, 16000, 1)
+    t0 = time.perf_counter()
+    ref = oracle.nucleus(off, adj, 2, 3, hier="def")
+    t_oracle = time.perf_counter() - t0
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    eager = []
+    for it in range(warmup + steps):
+        a = _ev()
+        res = nc.hierarchy(d_off, d_adj, 2, 3, method="auto")
+        b = _ev()
+        if it >= warmup:
+            eager.append(_ms(a, b))
+    core_equal = bool(np.array_equal(res["core"].cpu().numpy().view(np.uint32), ref["core"]))
+    o = nc.build_orientation(d_off, d_adj)
+    ri = nc.index_r_cliques(o, 2)
+    buf = nc.hierarchy_buffers(ri)
+    g = nc.capture_hierarchy(o, ri, 3, buf)
+    graph = []
+    for it in range(warmup + steps):
+        a = _ev()
+        g.replay()
+        b = _ev()
+        if it >= warmup:
+            graph.append(_ms(a, b))
+    st = buf["res"].cpu().numpy()
+    n_r = ri.n_r
+    nn = int(st[2])
+    same_graph = bool(st[0] == 0 and np.array_equal(buf["core"][:n_r].cpu().numpy().view(np.uint32), ref["core"]))
+    # canonical hierarchy: sorted leaf sets and labels, from the graph replay's tree and the oracle's
+    from oracle.brute import tree_to_nodes
+    par = buf["parent"][: n_r + nn].cpu().numpy()
+    got = tree_to_nodes(par[:n_r], par[n_r:], buf["label"][:nn].cpu().numpy().view(np.uint32))
+    want = tree_to_nodes(ref["leaf_node"], ref["node_parent"], ref["node_label"])
+    return {"metric": "exact (2,3) hierarchy latency", "unit": "ms",
+            "workload": "Erdos-Renyi G(n=2000, m=16000) seed 1, exact (2,3) hierarchy",
+            "n_r": int(ref["n_r"]), "n_s": int(ref["n_s"]), "nodes": len(want),
+            "eager_ms": _spread(eager), "graph_replay_ms": _spread(graph),
+            "cpu_baseline": {"value": 1000.0 * t_oracle, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": "the same graph and pair, core numbers + definitional hierarchy, once"},
+            "identical_to_oracle": bool(core_equal and same_graph and got == want)}
 
 
 def measure_cl4m(warmup: int = 1, steps: int = 5) -> dict:
@@ -748,6 +803,12 @@ def measure_approx(steps: int = 1) -> dict:
             "workload": "R-MAT 22 EF16 seed 4 (2,3); R-MAT 20 EF16 seed 3 (3,4); delta 0.1 and 0.5", "results": out}
 
 
+def run_er2k(args):
+    r = measure_er2k(max(args.warmup, 3), max(args.steps, 20))
+    print(json.dumps({"metric": r["metric"], "value": r["graph_replay_ms"]["median"], "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "config": r}), flush=True)
+
+
 def run_cl4m(args):
     line = {"metric": "s-clique counting time, learned vs degree work partition", "n_gpus": 1,
             "data": "synthetic", "higher_is_better": False}
@@ -855,6 +916,8 @@ def main():
     assert args.warmup >= 0 and args.steps >= 1
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "er2k":
+        run_er2k(args)
     elif args.workload == "cl4m":
         run_cl4m(args)
     elif args.workload == "batch512":
