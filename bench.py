@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--scale", type=int, default=18, help=argparse.SUPPRESS)
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
-    ap.add_argument("--workload", choices=["rmat18", "er2k", "cl4m", "batch512", "approx", "approx_hier", "peel1"],
+    ap.add_argument("--workload", choices=["rmat18", "er2k", "cl4m", "batch512", "approx", "approx_hier", "peel1",
+                                           "ablation"],
                     default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
@@ -803,6 +804,55 @@ def measure_approx(steps: int = 1) -> dict:
             "workload": "R-MAT 22 EF16 seed 4 (2,3); R-MAT 20 EF16 seed 3 (3,4); delta 0.1 and 0.5", "results": out}
 
 
+def run_ablation(args):
+    """NEXT-3, the paper's link ablation (§8's comparison of link-basic, link-efficient and the
+    two-phase hierarchy): on R-MAT <scale> EF16 seed 2, for each pair, the hierarchy time and the
+    union-find work of anh-bl (Alg. 4: unites over every level), anh-el (Alg. 3 + Alg. 5:
+    link-efficient calls and unites) and anh-te (§7.4), all three against the same core numbers
+    and the same node count."""
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    scale = args.scale if args.scale != 18 else 11
+    off, adj = gg.rmat(scale, 16, 2)
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    out = {}
+    for r, s in [(1, 2), (2, 3), (2, 4), (3, 4)]:
+        o = nc.build_orientation(d_off, d_adj)
+        ri = nc.index_r_cliques(o, r)
+        cnt, n_s = nc.count_s_cliques(o, ri, s)
+        rec = {"n_r": ri.n_r, "n_s": n_s}
+        pc = nc.peel_cores(o, ri, s, cnt)
+        for m in ("el", "te", "bl"):
+            for it in range(2):  # the second run is timed
+                a = _ev()
+                if m == "el":
+                    pk = nc.peel_and_link(o, ri, s, cnt, stats=True)
+                    parent, label, nn = nc.construct_tree(pk["core"], pk["uf"], pk["L"])
+                elif m == "te":
+                    parent, label, nn = nc.hierarchy_two_phase(o, ri, s, pc["core"])
+                else:
+                    parent, label, nn, un = nc.hierarchy_basic(o, ri, s, pc["core"])
+                b = _ev()
+            e = {"ms": _ms(a, b), "nodes": nn}
+            if m == "el":
+                e.update({"ms_note": "peel with link-efficient + construct-tree",
+                          "link_calls": pk["stats"]["link_calls"], "unites": pk["stats"]["unites"]})
+            elif m == "bl":
+                e.update({"ms_note": "link-basic + construct-tree-basic after the peel", "unites": un})
+            else:
+                e["ms_note"] = "two-phase hierarchy after the peel"
+            rec[m] = e
+        assert rec["el"]["nodes"] == rec["te"]["nodes"] == rec["bl"]["nodes"], rec
+        out["%d,%d" % (r, s)] = rec
+        del o, ri, cnt, pc
+    print(json.dumps({"metric": "hierarchy builders: time and union-find work", "unit": "ms", "n_gpus": 1,
+                      "data": "synthetic", "higher_is_better": False,
+                      "config": {"workload": "R-MAT scale %d EF16 seed 2" % scale, "pairs": out}}), flush=True)
+
+
 def run_er2k(args):
     r = measure_er2k(max(args.warmup, 3), max(args.steps, 20))
     print(json.dumps({"metric": r["metric"], "value": r["graph_replay_ms"]["median"], "unit": "ms",
@@ -918,6 +968,8 @@ def main():
         run_reference(args)
     elif args.workload == "er2k":
         run_er2k(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     elif args.workload == "cl4m":
         run_cl4m(args)
     elif args.workload == "batch512":
