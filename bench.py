@@ -218,7 +218,7 @@ def run_reference(args):
 # -------------------------------------------------------------------------------------------------
 
 def algorithmic_peel_bytes(stats: dict) -> int:
-    """Bytes the peel must move (the §8(d) count, from the peel's own device counters):
+    """Bytes the peel must move (the algorithmic byte count, from the peel's own device counters):
     B = 4 E_scan + 8 U_cnt + 16 P_hash + 8 N_link + 4 F, with E_scan = list elements read by the
     re-listing (adjacency, per-edge triangle lists and the out-lists expanded from them: every
     4-byte element read), U_cnt = count decrements (atomic read + write), P_hash = probes of the
@@ -805,7 +805,7 @@ def measure_approx(steps: int = 1) -> dict:
 
 
 def run_ablation(args):
-    """NEXT-3, the paper's link ablation (§8's comparison of link-basic, link-efficient and the
+    """The paper's link ablation (its §8 compares link-basic, link-efficient and the
     two-phase hierarchy): on R-MAT <scale> EF16 seed 2, for each pair, the hierarchy time and the
     union-find work of anh-bl (Alg. 4: unites over every level), anh-el (Alg. 3 + Alg. 5:
     link-efficient calls and unites) and anh-te (§7.4), all three against the same core numbers

@@ -69,7 +69,7 @@ typedef struct nh_peel_stats {
   uint64_t stamp_reads;        /* round stamps (or core numbers) of members read while re-listing */
 } nh_peel_stats;
 
-/* a1 -- Arb-Orient (Alg. 3, first step; §3 on O(alpha)-orientations).
+/* Orientation -- Arb-Orient (Alg. 3, first step; §3 on O(alpha)-orientations).
  * Builds the low out-degree orientation: u -> v iff (deg u, u) < (deg v, v) lexicographically;
  * out-lists keep ascending vertex order.  Also builds, per adjacency entry, the canonical id of
  * its edge, and the lexicographic edge list.  n >= 1; nnz = off[n] = 2m (read from the host
@@ -80,7 +80,7 @@ int nh_build_orientation(int64_t n, int64_t nnz, const int64_t* off, const int32
 int nh_oriented_info(const nh_oriented* o, int64_t* n, int64_t* m, int64_t* max_out, int64_t* max_deg);
 void nh_oriented_free(nh_oriented* o);
 
-/* a2 -- index the r-cliques (the keys of table U in Alg. 3).  r = 1: vertices; r = 2: edges;
+/* r-clique index -- the r-cliques (the keys of table U in Alg. 3).  r = 1: vertices; r = 2: edges;
  * r = 3: triangles, enumerated per lexicographic edge (a,b) as the common neighbours c > b, and
  * inserted into a device open-addressing hash table keyed by (edge id of (a,b), c); r = 4..6: the
  * same one level up -- per (r-1)-clique P in lexicographic order, the common neighbours c above
@@ -99,7 +99,7 @@ void nh_rindex_free(nh_rindex* ri);
  * round trip per round, and the hierarchy by link-efficient (Alg. 5) over every s-clique after the
  * peel followed by construct-tree.  nh_hierarchy_enqueue takes the specialised pairs only. */
 
-/* a3 -- rec-list-cliques (Alg. 3, count step): cnt[R] = number of s-cliques containing R
+/* Counting -- rec-list-cliques (Alg. 3, count step): cnt[R] = number of s-cliques containing R
  * (s-clique-degree, §3), for every r-clique R, found by recursive intersection of out-lists of
  * the orientation so that each s-clique is listed once.  cnt: uint32[n_r] (overwritten).
  * *n_s (host, may be NULL) receives the number of s-cliques.
@@ -108,7 +108,7 @@ void nh_rindex_free(nh_rindex* ri);
 int nh_count_s_cliques(const nh_oriented* o, const nh_rindex* ri, int s, uint32_t* cnt,
                        uint64_t* n_s, void* stream);
 
-/* a4-a8 -- the peeling loop of Alg. 3 interleaved with link-efficient (Alg. 5), in one
+/* Peel -- the peeling loop of Alg. 3 interleaved with link-efficient (Alg. 5), in one
  * persistent cooperative kernel.  Round t: k = max(k, min count over live r-cliques); the
  * frontier A is every live r-clique with count <= k; each R in A re-lists its s-cliques; an
  * s-clique whose members were all live at the start of the round dies now: its member of least
@@ -127,7 +127,7 @@ int nh_peel_and_link(const nh_oriented* o, const nh_rindex* ri, int s, const uin
                      uint32_t* core, uint32_t* round, int32_t* uf, int32_t* L, int link_mode,
                      nh_peel_stats* stats, void* stream);
 
-/* a9 -- construct-tree-efficient (Alg. 5): one node per union-find component, its parent the
+/* Tree -- construct-tree-efficient (Alg. 5): one node per union-find component, its parent the
  * node of find(L[root]); a node whose subtree holds a single r-clique is dropped and that
  * r-clique hangs from the dropped node's parent (§7.3 remark on single-child parents).
  * uf is compressed in place.  Outputs: parent int32[n_r + n_nodes] (entries 0..n_r-1: node of
@@ -156,7 +156,7 @@ int nh_construct_tree(int64_t n_r, const uint32_t* core, int32_t* uf, const int3
 int nh_construct_tree_noalloc(int64_t n_r, const uint32_t* core, int32_t* uf, const int32_t* L,
                               int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
-/* NEXT-3 / §7.2 -- link-basic and construct-tree-basic (Alg. 4), the ablation the paper measures
+/* Basic link (§7.2) -- link-basic and construct-tree-basic (Alg. 4), the ablation the paper measures
  * against link-efficient: one union-find per level 1..kmax (kmax * n_r int32 of device memory:
  * NH_ERR_OOM when that exceeds 80 % of the free memory); every s-clique unites its member of least
  * core with each other member in every level up to c_S (the definitional reading of §3, the same
@@ -203,7 +203,7 @@ int nh_hierarchy_two_phase(const nh_oriented* o, const nh_rindex* ri, int s, con
 int nh_label_hierarchy(const nh_oriented* o, const nh_rindex* ri, int s, const uint32_t* labels,
                        int32_t* parent, uint32_t* label, int64_t* n_nodes, void* stream);
 
-/* a10 -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
+/* Approximate peel -- approx-arb-nucleus (Alg. 2): buckets with upper ends t_i = floor(x_i),
  * x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta) (IEEE double, C = binom(s,r)); round t peels
  * every live r-clique with count <= t_i; after T = ceil(ln(max(n_r,2)) / log1p(delta/C)) + 1
  * rounds in one bucket, or when it is empty, the next bucket opens.  approx[R] = min(t_i,
@@ -220,7 +220,7 @@ int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double d
 int nh_link_pairs(int64_t n_r, const uint32_t* core, int32_t* uf, int32_t* L,
                   const int32_t* pairs, int64_t n_pairs, void* stream);
 
-/* a11 -- learned work estimator for the s-clique listing (rec-list-cliques) work.
+/* Work estimator -- a learned estimator for the s-clique listing (rec-list-cliques) work.
  * Work items are the out-edges (v -> a) of the orientation; a cost estimate per vertex orders the
  * items by decreasing cost, and the warps of the counting kernel take them in chunks from a shared
  * counter (largest first).  Counts do not depend on the schedule.  The estimator is an MLP NH_MLP_FEATURES -> 64 -> 64 -> 1 (ReLU),
@@ -249,7 +249,7 @@ int nh_mlp_predict(const float* feats, int64_t n, const uint16_t* weights, float
 int nh_count_s_cliques_partitioned(const nh_oriented* o, const nh_rindex* ri, int s, const float* vertex_cost,
                                    uint32_t* cnt, uint64_t* n_s, void* stream);
 
-/* a12 -- batches of graphs.  A batch is run as the disjoint union of its graphs (vertex ids of
+/* Batches of graphs.  A batch is run as the disjoint union of its graphs (vertex ids of
  * graph g shifted by vbase[g]), so one persistent peel launch serves all of them; s-cliques never
  * cross graphs, so every core number and hierarchy node equals that of its own graph, and the
  * r-cliques of graph g are the union's ids [rbase[g], rbase[g+1]).  The paper has no counterpart.
@@ -265,7 +265,7 @@ int nh_batch_union(const nh_graph_desc* graphs, int n_graphs, int64_t* off_out, 
 /* rbase int64[n_graphs+1] (host): first r-clique id of each graph of a union built from vbase */
 int nh_rindex_bases(const nh_rindex* ri, const int64_t* vbase, int n_graphs, int64_t* rbase, void* stream);
 
-/* a12 -- a batch as one library object.  nh_batch_prepare copies the graphs into their disjoint
+/* A batch as one library object.  nh_batch_prepare copies the graphs into their disjoint
  * union (owned by the handle), builds its orientation and its r-clique index (r = 1, 2, 3), and
  * returns *n_r (host) = the union's r-cliques; it synchronises `stream` (sizes come back to the
  * host).  nh_batch_run then enqueues, for one s, exactly what nh_hierarchy_enqueue does on the

@@ -1,4 +1,4 @@
-// nh_batch.cu -- a12: a batch of graphs as one disjoint union, so that one persistent peel launch
+// nh_batch.cu -- a batch of graphs as one disjoint union, so that one persistent peel launch
 // serves every graph of the batch (frontiers of all graphs share each round).  s-cliques never
 // cross graphs, so every core number and every hierarchy node is that of its own graph; the
 // union's lexicographic r-clique order lists graph 0's r-cliques first, then graph 1's, and so on.

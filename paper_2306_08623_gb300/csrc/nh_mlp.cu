@@ -1,4 +1,4 @@
-// nh_mlp.cu -- a11: the learned work estimator and the cost-driven schedule of the s-clique
+// nh_mlp.cu -- the learned work estimator and the cost-driven schedule of the s-clique
 // listing work.  A small MLP (8 features -> 64 -> 64 -> 1, ReLU; BF16 weights, FP32
 // accumulation) is trained on per-vertex listing costs that the counting kernel measures, and
 // predicts cost per vertex; the out-edge work items are then ordered by decreasing predicted cost

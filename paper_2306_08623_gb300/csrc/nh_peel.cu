@@ -1,4 +1,4 @@
-// nh_peel.cu -- a4..a8 and a10: the peeling loop of Alg. 3 (exact, interleaved with
+// nh_peel.cu -- the peeling loop of Alg. 3 (exact, interleaved with
 // link-efficient of Alg. 5) and of Alg. 2 (approximate), as one persistent cooperative kernel
 // per call; plus link-efficient on a batch of calls (nh_link_pairs).
 //
