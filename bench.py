@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
     ap.add_argument("--workload", choices=["rmat18", "er2k", "cl4m", "batch512", "approx", "approx_hier", "peel1",
-                                           "ablation"],
+                                           "ablation", "roundtrace"],
                     default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
@@ -853,6 +853,62 @@ def run_ablation(args):
                       "config": {"workload": "R-MAT scale %d EF16 seed 2" % scale, "pairs": out}}), flush=True)
 
 
+def run_roundtrace(args):
+    """The cores-only peel of one pair of R-MAT <scale> EF16 seed 2 with the library's round trace
+    (nh_debug_round_log): per round the frontier size and block 0's device timer at the round's
+    end and, for the (2,4) triangle-list re-listing, at its start, after its split into sub-tasks
+    and after its warp phase.  Prints round-duration statistics by frontier size and the median
+    phase times of rounds with fewer than 16 frontier r-cliques."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    lib = nc.lib()
+    r, s = (int(x) for x in args.pair.split(","))
+    off, adj = gg.rmat(args.scale, 16, 2)
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    o = nc.build_orientation(d_off, d_adj)
+    ri = nc.index_r_cliques(o, r)
+    cnt, _ = nc.count_s_cliques(o, ri, s)
+    nc.peel_cores(o, ri, s, cnt)  # warm-up
+    cap = 1 << 17
+    log = torch.zeros(8 * cap, dtype=torch.int64, device="cuda")
+    if lib.nh_debug_round_log(ctypes.c_void_p(log.data_ptr()), cap) != 0:
+        raise RuntimeError("round trace refused")
+    try:
+        a = _ev()
+        pk = nc.peel_cores(o, ri, s, cnt, stats=True)
+        b = _ev()
+    finally:
+        lib.nh_debug_round_log(None, 0)
+    n = min(int(pk["stats"]["rounds"]), cap)
+    L = log.cpu().numpy().reshape(cap, 8)[:n]
+    fr = (L[1:, 0].view(np.uint64) >> np.uint64(32)).astype(np.int64)
+    end = L[:, 1]
+    dur = np.diff(end).astype(np.float64)
+    buckets = {}
+    for lo, hi in [(1, 16), (16, 256), (256, 4096), (4096, 1 << 40)]:
+        m = (fr >= lo) & (fr < hi)
+        if m.any():
+            buckets["%d-%d" % (lo, hi - 1)] = {"rounds": int(m.sum()), "ms": float(dur[m].sum() / 1e6),
+                                               "median_us": float(np.median(dur[m]) / 1e3)}
+    small = np.nonzero((fr < 16) & (L[1:, 4] > 0))[0] + 1
+    phases = None
+    if len(small):
+        med = lambda x: float(np.median(x) / 1e3)
+        phases = {"to_relist_start_us": med(L[small, 4] - end[small - 1]), "split_us": med(L[small, 5] - L[small, 4]),
+                  "warp_phase_us": med(L[small, 6] - L[small, 5]), "to_round_end_us": med(end[small] - L[small, 7])}
+    print(json.dumps({"metric": "peel round durations", "unit": "us", "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": "R-MAT scale %d EF16 seed 2 (%d,%d), cores-only peel" % (args.scale, r, s),
+                                 "launch_ms": _ms(a, b), "rounds": int(pk["stats"]["rounds"]),
+                                 "duration_percentiles_us": [float(x) for x in
+                                                             np.percentile(dur, [5, 25, 50, 75, 95, 99]) / 1e3],
+                                 "by_frontier": buckets, "small_round_phases": phases}}), flush=True)
+
+
 def run_er2k(args):
     r = measure_er2k(max(args.warmup, 3), max(args.steps, 20))
     print(json.dumps({"metric": r["metric"], "value": r["graph_replay_ms"]["median"], "unit": "ms",
@@ -970,6 +1026,8 @@ def main():
         run_er2k(args)
     elif args.workload == "ablation":
         run_ablation(args)
+    elif args.workload == "roundtrace":
+        run_roundtrace(args)
     elif args.workload == "cl4m":
         run_cl4m(args)
     elif args.workload == "batch512":
