@@ -581,9 +581,9 @@ def hierarchy(off: torch.Tensor, adj: torch.Tensor, r: int, s: int, link_mode: s
     and hierarchy.  method "el": link-efficient interleaved with the peel, then construct-tree
     (Alg. 3 + Alg. 5); "te": core numbers, then the two-phase hierarchy (§7.4, definitional
     reading only); "bl": core numbers, then link-basic and construct-tree-basic (Alg. 4, the
-    ablation); "auto": the builder measured faster on a GB300 (R-MAT 18, peel + hierarchy):
-    "te" for every pair but (3,4), whose linking peel is faster than its cores-only peel plus the
-    two-phase hierarchy; "el" for the pair rule (link_mode "pair"), which only "el" follows.
+    ablation); "auto": "te" for (1,2), (2,3), (2,4), where it is the faster builder on a GB300
+    (R-MAT 18, peel + hierarchy), "el" for (3,4), where the two are level, and for the pair rule
+    (link_mode "pair"), which only "el" follows.
     Pairs beyond (1,2), (1,3), (2,3), (2,4), (3,4) (any r < s <= 7) run the generic path, where
     "el" and "te" both link over every s-clique after the peel."""
     if method == "auto":
