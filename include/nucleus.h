@@ -213,6 +213,15 @@ int nh_approx_nucleus(const nh_oriented* o, const nh_rindex* ri, int s, double d
                       const uint32_t* cnt, uint32_t* approx, uint32_t* round,
                       nh_peel_stats* stats, void* stream);
 
+/* The schedule both approximate peels use (host only, no device work): Alg. 2's bucket upper ends
+ * t_i = floor(x_i), x_0 = (C + delta)(1 + delta), x_{i+1} = x_i (1 + delta) in IEEE double
+ * (saturating at 2^32 - 1), written to out (host uint32[cap]) up to and including the first end
+ * >= max_count, *n = how many (at most cap); and the round cap per bucket
+ * T = ceil(ln(max(n_r, 2)) / log1p(delta / C)) + 1 (the constant Alg. 2 leaves open).  C = C(s,r).
+ * Errors: NH_ERR_INVALID (C < 1, delta <= 0, null pointers, cap < 1, n_r < 0). */
+int nh_approx_thresholds(int C, double delta, uint32_t max_count, uint32_t* out, int cap, int* n);
+int nh_approx_round_cap(int C, double delta, int64_t n_r, uint32_t* T);
+
 /* link-efficient (Alg. 5) applied to a batch of calls, one device thread per call, all
  * concurrent: pairs int32[2*n_pairs] (R, Q), core uint32[n_r] (ND), uf / L int32[n_r] updated
  * in place.  The building block of nh_peel_and_link, exported for direct use and testing.

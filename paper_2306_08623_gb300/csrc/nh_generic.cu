@@ -751,8 +751,7 @@ int nh_peel_generic(bool exact, const nh_oriented* o, const nh_rindex* ri, int s
   k_gen_init<<<nh_blocks_for(n_r, 256, 152 * 32), 256, 0, st>>>(n_r, cnt0, cnt, round, val, alive[0]);
   nh_note_launch();
   cudaMemsetAsync(status, 0, sizeof(int), st);
-  // Alg. 2's bucket ends t_i = floor(x_i), x_0 = (C+delta)(1+delta), x_{i+1} = x_i (1+delta), and the
-  // round cap T per bucket
+  // Alg. 2's bucket ends and round cap per bucket (nh_approx_table / nh_approx_cap, nh_peel.cu)
   std::vector<uint32_t> thr;
   uint32_t T = 0;
   if (!exact) {
@@ -765,16 +764,9 @@ int nh_peel_generic(bool exact, const nh_oriented* o, const nh_rindex* ri, int s
     cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
     nh_free(dmax, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto done; }
-    double x = ((double)C + delta) * (1.0 + delta);
-    for (int i = 0; i < (1 << 16); i++) {
-      const double f = std::floor(x);
-      const uint32_t tv = (f >= 4294967295.0) ? 4294967295u : (uint32_t)f;
-      thr.push_back(tv);
-      if (tv >= hmax) break;
-      x = x * (1.0 + delta);
-    }
-    const double nn = (double)(n_r > 2 ? n_r : 2);
-    T = (uint32_t)std::ceil(std::log(nn) / std::log1p(delta / (double)C)) + 1u;
+    thr.resize(1 << 16);
+    thr.resize((size_t)nh_approx_table(C, delta, hmax, thr.data(), 1 << 16));
+    T = nh_approx_cap(C, delta, n_r);
   }
   {
     RelistArgs R{};

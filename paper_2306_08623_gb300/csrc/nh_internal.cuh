@@ -278,6 +278,9 @@ static inline int nh_binom(int n, int k) {
 static inline bool nh_supported(int r, int s) {
   return (r == 1 && (s == 2 || s == 3)) || (r == 2 && (s == 3 || s == 4)) || (r == 3 && s == 4);
 }
+// Alg. 2's bucket ends (at most cap, returns how many) and round cap (nh_peel.cu; host only)
+int nh_approx_table(int C, double delta, uint32_t max_count, uint32_t* out, int cap);
+uint32_t nh_approx_cap(int C, double delta, int64_t n_r);
 // pairs served by the generic path (nh_generic.cu): every other 1 <= r < s <= 7
 static inline bool nh_generic_pair(int r, int s) { return r >= 1 && s > r && s <= 7 && !nh_supported(r, s); }
 // generic path entry points (nh_generic.cu)

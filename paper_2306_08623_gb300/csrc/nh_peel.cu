@@ -35,6 +35,39 @@ static int g_peel_list_hash = 0;      // set by nh_set_peel_list_hash (0 off, 1 
 static float g_split_per_warp = 1.0f;  // set by nh_set_relist_split
 static int g_split_wgrain = 128, g_split_bgrain = 1024, g_split_len_mult = 0;
 
+// Alg. 2's schedule (readings R9, R10): bucket upper ends t_i = floor(x_i) with x_0 = (C+delta)(1+delta)
+// and x_{i+1} = x_i (1+delta) in IEEE double, up to the first end >= max_count (at most cap ends);
+// the round cap T = ceil(ln(max(n_r, 2)) / log1p(delta / C)) + 1.  Shared by both peels.
+int nh_approx_table(int C, double delta, uint32_t max_count, uint32_t* out, int cap) {
+  double x = ((double)C + delta) * (1.0 + delta);
+  int k = 0;
+  while (k < cap) {
+    const double f = std::floor(x);
+    const uint32_t tv = (f >= 4294967295.0) ? 4294967295u : (uint32_t)f;
+    out[k++] = tv;
+    if (tv >= max_count) break;
+    x = x * (1.0 + delta);
+  }
+  return k;
+}
+
+uint32_t nh_approx_cap(int C, double delta, int64_t n_r) {
+  const double nn = (double)(n_r > 2 ? n_r : 2);
+  return (uint32_t)std::ceil(std::log(nn) / std::log1p(delta / (double)C)) + 1u;
+}
+
+extern "C" int nh_approx_thresholds(int C, double delta, uint32_t max_count, uint32_t* out, int cap, int* n) {
+  if (C < 1 || !(delta > 0.0) || !out || cap < 1 || !n) return NH_ERR_INVALID;
+  *n = nh_approx_table(C, delta, max_count, out, cap);
+  return NH_OK;
+}
+
+extern "C" int nh_approx_round_cap(int C, double delta, int64_t n_r, uint32_t* T) {
+  if (C < 1 || !(delta > 0.0) || n_r < 0 || !T) return NH_ERR_INVALID;
+  *T = nh_approx_cap(C, delta, n_r);
+  return NH_OK;
+}
+
 namespace nhp {
 
 __global__ void k_peel_init(int64_t n_r, const uint32_t* __restrict__ cnt0, uint32_t* __restrict__ cnt,
@@ -318,16 +351,9 @@ int run_peel(bool exact, const nh_oriented* o, const nh_rindex* ri, int s, const
     unsigned int hmax = 0;
     cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = NH_ERR_CUDA; goto cleanup; }
-    double x = ((double)C + delta) * (1.0 + delta);
-    for (int i = 0; i < (1 << 16); i++) {
-      const double f = std::floor(x);
-      const uint32_t tv = (f >= 4294967295.0) ? 4294967295u : (uint32_t)f;
-      thr_host.push_back(tv);
-      if (tv >= hmax) break;
-      x = x * (1.0 + delta);
-    }
-    const double nn = (double)(n_r > 2 ? n_r : 2);
-    A.T = (uint32_t)std::ceil(std::log(nn) / std::log1p(delta / (double)C)) + 1u;
+    thr_host.resize(1 << 16);
+    thr_host.resize((size_t)nh_approx_table(C, delta, hmax, thr_host.data(), 1 << 16));
+    A.T = nh_approx_cap(C, delta, n_r);
     A.n_thr = (int)thr_host.size();
     if ((rc = nh_alloc(&thr_dev, A.n_thr, st))) goto cleanup;
     if (cudaMemcpyAsync(thr_dev, thr_host.data(), sizeof(uint32_t) * thr_host.size(), cudaMemcpyHostToDevice, st) !=
