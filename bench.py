@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--pair", default="2,4", help="(r,s) for --workload peel1")
     ap.add_argument("--method", choices=["el", "te", "auto"], default="auto", help="hierarchy for --workload peel1")
     ap.add_argument("--workload", choices=["rmat18", "er2k", "cl4m", "batch512", "approx", "approx_hier", "peel1",
-                                           "ablation", "roundtrace"],
+                                           "ablation", "roundtrace", "generic"],
                     default="rmat18",
                     help="rmat18: the headline step (default); cl4m: learned vs degree work partition on "
                          "Chung-Lu n=4M; batch512: 512 graphs batched vs one by one; approx: approximate vs "
@@ -853,6 +853,41 @@ def run_ablation(args):
                       "config": {"workload": "R-MAT scale %d EF16 seed 2" % scale, "pairs": out}}), flush=True)
 
 
+def run_generic(args):
+    """Pairs beyond the benchmark's five (the generic path) on R-MAT <scale> EF16 seed 2 (default
+    scale 11): index, counting, cores-only peel and the whole hierarchy ("el": peel, then
+    link-efficient over every s-clique, then construct-tree), one warm-up run then one timed run
+    each."""
+    import torch
+
+    import paper_2306_08623_gb300.nucleus as nc
+    from paper_2306_08623_gb300 import graphgen as gg
+    nc.lib()
+    scale = args.scale if args.scale != 18 else 11
+    off, adj = gg.rmat(scale, 16, 2)
+    d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
+    o = nc.build_orientation(d_off, d_adj)
+    out = {}
+    for r, s in [(1, 4), (2, 5), (3, 5), (4, 5), (1, 5), (2, 6)]:
+        rec = {}
+        for it in range(2):
+            a = _ev()
+            ri = nc.index_r_cliques(o, r)
+            b = _ev()
+            cnt, n_s = nc.count_s_cliques(o, ri, s)
+            c = _ev()
+            pk = nc.peel_cores(o, ri, s, cnt, stats=True)
+            d = _ev()
+            h = nc.hierarchy(d_off, d_adj, r, s, method="el")
+            e = _ev()
+            rec = {"n_r": ri.n_r, "n_s": n_s, "index_ms": _ms(a, b), "count_ms": _ms(b, c), "peel_ms": _ms(c, d),
+                   "rounds": pk["stats"]["rounds"], "hierarchy_total_ms": _ms(d, e), "nodes": h["n_nodes"]}
+            del h, pk, cnt, ri
+        out["%d,%d" % (r, s)] = rec
+    print(json.dumps({"metric": "generic-path pairs", "unit": "ms", "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": "R-MAT scale %d EF16 seed 2" % scale, "pairs": out}}), flush=True)
+
+
 def run_roundtrace(args):
     """The cores-only peel of one pair of R-MAT <scale> EF16 seed 2 with the library's round trace
     (nh_debug_round_log): per round the frontier size and block 0's device timer at the round's
@@ -1028,6 +1063,8 @@ def main():
         run_ablation(args)
     elif args.workload == "roundtrace":
         run_roundtrace(args)
+    elif args.workload == "generic":
+        run_generic(args)
     elif args.workload == "cl4m":
         run_cl4m(args)
     elif args.workload == "batch512":
