@@ -855,15 +855,16 @@ def run_ablation(args):
 
 def run_generic(args):
     """Pairs beyond the benchmark's five (the generic path) on R-MAT <scale> EF16 seed 2 (default
-    scale 11): index, counting, cores-only peel and the whole hierarchy ("el": peel, then
+    scale 9): index, counting, cores-only peel and the whole hierarchy ("el": peel, then
     link-efficient over every s-clique, then construct-tree), one warm-up run then one timed run
-    each."""
+    each.  The generic re-listing gives each r-clique's candidate search to one warp, so pairs with
+    r = 1 slow down steeply with hub degree (at scale 11 the run takes minutes)."""
     import torch
 
     import paper_2306_08623_gb300.nucleus as nc
     from paper_2306_08623_gb300 import graphgen as gg
     nc.lib()
-    scale = args.scale if args.scale != 18 else 11
+    scale = args.scale if args.scale != 18 else 9
     off, adj = gg.rmat(scale, 16, 2)
     d_off, d_adj = torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda()
     o = nc.build_orientation(d_off, d_adj)
